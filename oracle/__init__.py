@@ -1,0 +1,204 @@
+"""FP64 CPU oracle for the reflection-geometry multislice model (arxiv 2212.01253).
+
+TEST INFRASTRUCTURE ONLY.  This package is imported by ``tests/``, by
+``__graft_entry__.smoke()`` and by the CPU-baseline / reference leg of
+``bench.py``; the product package never imports it and it never imports the
+product package.  It shares no code with the CUDA path.
+
+The numerical work lives in ``mslice_oracle.c`` (plain C99 + OpenMP, double
+precision, own DFT/FFT); this module compiles it with gcc on first use and
+wraps it with ctypes.  Every entry point follows the steps written out in the
+C file's header:
+
+* Eq. 1 (Sec. 1): transmission exp(-i k Delta (delta - i beta)) then the
+  paraxial Fresnel propagator exp(-i Delta (k_y^2 + k_z^2) / 2k) in Fourier
+  space, slice after slice.
+* Fig. 1a: the last exit wave is Fourier transformed and squared.
+* Eq. 4 (Sec. 4.1): squared error of amplitudes, here summed (no 1/N).
+* The gradient is the exact adjoint of those steps (the paper used autograd).
+
+Parity is pinned by ``tests/test_oracle_pins.py`` (closed forms, physics,
+brute force, finite differences); no oracle function is "parity unpinned".
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "mslice_oracle.c")
+_BUILD_DIR = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD_DIR, "libmslice_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle shared library (gcc, -O2, OpenMP, IEEE math)."""
+    os.makedirs(_BUILD_DIR, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + ".tmp%d" % os.getpid()
+    cmd = ["gcc", "-std=c11", "-O2", "-fopenmp", "-fPIC", "-shared", "-Wall",
+           "-o", tmp, _SRC, "-lm"]
+    subprocess.check_call(cmd)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class OrcParams(ctypes.Structure):
+    _fields_ = [
+        ("wavelength_nm", ctypes.c_double),
+        ("slice_nm", ctypes.c_double),
+        ("dy_nm", ctypes.c_double),
+        ("dz_nm", ctypes.c_double),
+        ("ny", ctypes.c_int32),
+        ("nz", ctypes.c_int32),
+        ("ns", ctypes.c_int32),
+        ("nw", ctypes.c_int32),
+        ("alpha_i_rad", ctypes.POINTER(ctypes.c_double)),
+        ("force_naive_dft", ctypes.c_int32),
+        ("exit_wave", ctypes.c_int32),
+    ]
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            vp, dp = ctypes.c_void_p, ctypes.POINTER(OrcParams)
+            lib.orc_forward.argtypes = [dp, vp, vp, vp, vp]
+            lib.orc_adjoint.argtypes = [dp, vp, vp, vp, vp]
+            lib.orc_loss_grad.argtypes = [dp, vp, vp, vp, ctypes.c_double, vp, vp, vp]
+            lib.orc_propagator_1d.argtypes = [dp, vp, vp]
+            lib.orc_dft1d.argtypes = [ctypes.c_int, vp, ctypes.c_int, ctypes.c_int]
+            lib.orc_dft2d.argtypes = [ctypes.c_int, ctypes.c_int, vp, ctypes.c_int, ctypes.c_int]
+            for f in ("orc_forward", "orc_adjoint", "orc_loss_grad", "orc_propagator_1d",
+                      "orc_dft1d", "orc_dft2d", "orc_num_threads"):
+                getattr(lib, f).restype = ctypes.c_int
+            _lib = lib
+    return _lib
+
+
+def num_threads() -> int:
+    """OpenMP threads the oracle runs with."""
+    return int(_load().orc_num_threads())
+
+
+class Geometry:
+    """Grid and beam: lambda, Delta, dy, dz, (Ny, Nz, Ns) and the incidence angles."""
+
+    def __init__(self, ny, nz, ns, wavelength_nm=0.155, slice_nm=20.0, dy_nm=2.0,
+                 dz_nm=2.0, alpha_i_deg=(0.3,)):
+        self.ny, self.nz, self.ns = int(ny), int(nz), int(ns)
+        self.wavelength_nm = float(wavelength_nm)
+        self.slice_nm = float(slice_nm)
+        self.dy_nm, self.dz_nm = float(dy_nm), float(dz_nm)
+        self.alpha_i_rad = np.deg2rad(np.atleast_1d(np.asarray(alpha_i_deg, dtype=np.float64)))
+
+    @property
+    def nw(self):
+        return int(self.alpha_i_rad.size)
+
+    def _params(self, naive=False, exit_wave=False):
+        self._alpha_keep = np.ascontiguousarray(self.alpha_i_rad, dtype=np.float64)
+        return OrcParams(self.wavelength_nm, self.slice_nm, self.dy_nm, self.dz_nm,
+                         self.ny, self.nz, self.ns, self.nw,
+                         self._alpha_keep.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                         int(bool(naive)), int(bool(exit_wave)))
+
+
+def _c128(a, shape):
+    a = np.ascontiguousarray(a, dtype=np.complex128)
+    if a.shape != tuple(shape):
+        raise ValueError("expected shape %s, got %s" % (shape, a.shape))
+    return a
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _rc(rc, name):
+    if rc != 0:
+        raise RuntimeError("%s failed with code %d" % (name, rc))
+
+
+def forward(geo: Geometry, vol, probe=None, naive=False, exit_wave=False, return_field=False):
+    """Detector intensity I [nw][nz][ny] (and Psi, or phi_Ns with exit_wave)."""
+    vol = _c128(vol, (geo.ns, geo.nz, geo.ny))
+    if probe is not None:
+        probe = _c128(probe, (geo.nw, geo.nz, geo.ny))
+    shape = (geo.nw, geo.nz, geo.ny)
+    inten = np.zeros(shape, np.float64)
+    field = np.zeros(shape, np.complex128) if (return_field or exit_wave) else None
+    p = geo._params(naive, exit_wave)
+    _rc(_load().orc_forward(ctypes.byref(p), _ptr(vol), _ptr(probe), _ptr(inten), _ptr(field)),
+        "orc_forward")
+    if exit_wave:
+        return field
+    return (inten, field) if return_field else inten
+
+
+def adjoint(geo: Geometry, vol, g_psi, probe=None, naive=False):
+    """grad = dL/ddelta + i dL/dbeta [ns][nz][ny] for a detector gradient g_psi."""
+    vol = _c128(vol, (geo.ns, geo.nz, geo.ny))
+    g_psi = _c128(g_psi, (geo.nw, geo.nz, geo.ny))
+    if probe is not None:
+        probe = _c128(probe, (geo.nw, geo.nz, geo.ny))
+    grad = np.zeros((geo.ns, geo.nz, geo.ny), np.complex128)
+    p = geo._params(naive)
+    _rc(_load().orc_adjoint(ctypes.byref(p), _ptr(vol), _ptr(probe), _ptr(g_psi), _ptr(grad)),
+        "orc_adjoint")
+    return grad
+
+
+def loss_grad(geo: Geometry, vol, meas_amp, scale, probe=None, naive=False,
+              return_intensity=False):
+    """(L, grad) with L = sum (sqrt(scale I) - meas_amp)^2, grad as in adjoint()."""
+    vol = _c128(vol, (geo.ns, geo.nz, geo.ny))
+    meas_amp = np.ascontiguousarray(meas_amp, dtype=np.float64)
+    if meas_amp.shape != (geo.nw, geo.nz, geo.ny):
+        raise ValueError("meas_amp shape %s" % (meas_amp.shape,))
+    if probe is not None:
+        probe = _c128(probe, (geo.nw, geo.nz, geo.ny))
+    grad = np.zeros((geo.ns, geo.nz, geo.ny), np.complex128)
+    inten = np.zeros((geo.nw, geo.nz, geo.ny), np.float64)
+    loss = ctypes.c_double(0.0)
+    p = geo._params(naive)
+    _rc(_load().orc_loss_grad(ctypes.byref(p), _ptr(vol), _ptr(probe), _ptr(meas_amp),
+                              float(scale), ctypes.cast(ctypes.byref(loss), ctypes.c_void_p),
+                              _ptr(grad), _ptr(inten)), "orc_loss_grad")
+    if return_intensity:
+        return loss.value, grad, inten
+    return loss.value, grad
+
+
+def propagator_1d(geo: Geometry):
+    """(P_y [ny], P_z [nz]) with P = exp(-i Delta k^2 / 2k)."""
+    py = np.zeros(geo.ny, np.complex128)
+    pz = np.zeros(geo.nz, np.complex128)
+    p = geo._params()
+    _rc(_load().orc_propagator_1d(ctypes.byref(p), _ptr(py), _ptr(pz)), "orc_propagator_1d")
+    return py, pz
+
+
+def dft1d(x, sign=-1, naive=False):
+    """Unnormalised 1-D DFT with kernel exp(sign * 2 pi i m k / n)."""
+    x = np.array(x, dtype=np.complex128, copy=True)
+    _rc(_load().orc_dft1d(x.size, _ptr(x), int(sign), int(bool(naive))), "orc_dft1d")
+    return x
+
+
+def dft2d(x, sign=-1, naive=False):
+    """Unnormalised 2-D DFT of x[nz][ny]."""
+    x = np.array(x, dtype=np.complex128, copy=True)
+    nz, ny = x.shape
+    _rc(_load().orc_dft2d(ny, nz, _ptr(x), int(sign), int(bool(naive))), "orc_dft2d")
+    return x

@@ -1,0 +1,322 @@
+"""Pins of the FP64 oracle against what the physics and mathematics fix.
+
+None of these re-types the oracle's own formula: each compares it with an
+independent closed form, a library routine on a special case, brute force, or
+a finite-difference / transpose identity, chosen so that a dropped term, a
+wrong sign, a wrong scale or a transposed axis fails at least one of them.
+"""
+import numpy as np
+import pytest
+
+import cssi_inputs as ci
+
+pytestmark = pytest.mark.filterwarnings("ignore")
+
+LAM = 0.155
+K = 2 * np.pi / LAM
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.ravel(a - b)) / np.linalg.norm(np.ravel(b)))
+
+
+# --------------------------------------------------------------------------
+# DFT: brute force and library special cases
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("n", [1, 2, 4, 8, 16, 32, 64, 128, 256, 512, 1024])
+def test_fft_equals_naive_dft(oracle_lib, n):
+    rng = np.random.default_rng(n)
+    x = rng.normal(size=n) + 1j * rng.normal(size=n)
+    for sign in (-1, 1):
+        a = oracle_lib.dft1d(x, sign=sign, naive=False)
+        b = oracle_lib.dft1d(x, sign=sign, naive=True)
+        assert np.abs(a - b).max() <= 1e-13 * max(1.0, np.abs(b).max())
+
+
+@pytest.mark.parametrize("n", [2, 8, 64, 512])
+def test_dft_matches_numpy(oracle_lib, n):
+    """Library special case: forward kernel e^{-i}, unnormalised; backward e^{+i}."""
+    rng = np.random.default_rng(7 + n)
+    x = rng.normal(size=n) + 1j * rng.normal(size=n)
+    assert np.abs(oracle_lib.dft1d(x, -1) - np.fft.fft(x)).max() < 1e-12 * n
+    assert np.abs(oracle_lib.dft1d(x, +1) - n * np.fft.ifft(x)).max() < 1e-12 * n
+
+
+@pytest.mark.parametrize("shape", [(4, 8), (32, 32), (16, 64), (64, 16)])
+def test_dft2_naive_vs_fft_and_numpy(oracle_lib, shape):
+    rng = np.random.default_rng(sum(shape))
+    x = rng.normal(size=shape) + 1j * rng.normal(size=shape)
+    a = oracle_lib.dft2d(x, naive=False)
+    b = oracle_lib.dft2d(x, naive=True)
+    assert rel(a, b) < 1e-13
+    assert rel(a, np.fft.fft2(x)) < 1e-13
+
+
+def test_single_vacuum_slice_is_unitary_fft2(oracle_lib):
+    """Ns=1, empty volume: Psi = fft2(probe, norm='ortho'), natural order."""
+    ny, nz = 32, 16
+    geo = oracle_lib.Geometry(ny, nz, 1)
+    probe = ci.random_probe(3, 1, ny, nz).astype(np.complex128)
+    vol = np.zeros((1, nz, ny), np.complex128)
+    I, psi = oracle_lib.forward(geo, vol, probe=probe, return_field=True)
+    ref = np.fft.fft2(probe[0], norm="ortho")
+    assert np.abs(psi[0] - ref).max() < 1e-13
+    assert np.abs(I[0] - np.abs(ref) ** 2).max() < 1e-13
+
+
+# --------------------------------------------------------------------------
+# Free-space Gaussian beam against the analytic paraxial solution
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("ny,nz,dy,dz", [(64, 64, 2.0, 2.0), (64, 128, 2.0, 1.0), (1, 128, 2.0, 1.0)])
+def test_gaussian_free_space(oracle_lib, ny, nz, dy, dz):
+    """phi0 = exp(-r^2/w0^2) propagates over L = Ns*Delta to
+    (w0^2/W^2)^{d/2} exp(-r^2/W^2), W^2 = w0^2 + 2iL/k (d = number of transverse axes).
+
+    Checked on the complex exit wave, so the propagator's scale Delta/2k, its
+    sign, the k-grid of each axis (dy vs dz) and the FFT normalisation all
+    enter."""
+    ns, delta, w0 = 32, 20.0, 10.0
+    L = ns * delta
+    geo = oracle_lib.Geometry(ny, nz, ns, slice_nm=delta, dy_nm=dy, dz_nm=dz, alpha_i_deg=(0.0,))
+    probe = ci.gaussian_probe(ny, nz, dy, dz, w0)[None]
+    vol = np.zeros((ns, nz, ny), np.complex128)
+    out = oracle_lib.forward(geo, vol, probe=probe, exit_wave=True)[0]
+    z = (np.arange(nz) - nz // 2) * dz
+    y = (np.arange(ny) - ny // 2) * dy
+    zz, yy = np.meshgrid(z, y, indexing="ij")
+    W2 = w0 ** 2 + 2j * L / K
+    d = 1 if ny == 1 else 2
+    r2 = zz ** 2 + (0 if ny == 1 else yy ** 2)
+    ref = (w0 ** 2 / W2) ** (d / 2) * np.exp(-r2 / W2)
+    assert np.abs(out - ref).max() < 1e-10
+    # and the wrong-sign solution is far away (the pin can fail)
+    bad = (w0 ** 2 / np.conj(W2)) ** (d / 2) * np.exp(-r2 / np.conj(W2))
+    assert np.abs(out - bad).max() > 1e-2
+
+
+# --------------------------------------------------------------------------
+# Invariants and uniform media
+# --------------------------------------------------------------------------
+def test_norm_conservation_without_absorption(oracle_lib):
+    ny, nz, ns = 32, 64, 12
+    geo = oracle_lib.Geometry(ny, nz, ns, alpha_i_deg=(0.2, 0.4))
+    vol = ci.random_volume(1, ny, nz, ns).real.astype(np.complex128) * 20  # beta = 0
+    probe = ci.random_probe(2, 2, ny, nz).astype(np.complex128)
+    I = oracle_lib.forward(geo, vol, probe=probe)
+    for w in range(2):
+        assert abs(I[w].sum() / (np.abs(probe[w]) ** 2).sum() - 1) < 1e-12
+    # absorption removes power
+    vol2 = vol + 1j * 1e-5
+    I2 = oracle_lib.forward(geo, vol2, probe=probe)
+    assert I2.sum() < I.sum() * (1 - 1e-3)
+
+
+def test_uniform_medium(oracle_lib):
+    """Uniform delta: only a global phase, I unchanged.  Uniform beta:
+    I scales by exp(-2 k Delta beta Ns)."""
+    ny, nz, ns, delta = 32, 32, 10, 20.0
+    geo = oracle_lib.Geometry(ny, nz, ns, slice_nm=delta)
+    probe = ci.random_probe(5, 1, ny, nz).astype(np.complex128)
+    vac = oracle_lib.forward(geo, np.zeros((ns, nz, ny)), probe=probe)
+    d = oracle_lib.forward(geo, np.full((ns, nz, ny), 3e-5 + 0j), probe=probe)
+    assert rel(d, vac) < 1e-12
+    beta = 2e-6
+    b = oracle_lib.forward(geo, np.full((ns, nz, ny), 1j * beta), probe=probe)
+    assert rel(b, vac * np.exp(-2 * K * delta * beta * ns)) < 1e-12
+
+
+def test_periodic_shift_and_mirror_in_y(oracle_lib):
+    ny, nz, ns = 32, 32, 8
+    geo = oracle_lib.Geometry(ny, nz, ns)
+    vol = ci.random_volume(9, ny, nz, ns, scale=30).astype(np.complex128)
+    probe = ci.random_probe(9, 1, ny, nz).astype(np.complex128)
+    I = oracle_lib.forward(geo, vol, probe=probe)[0]
+    Is = oracle_lib.forward(geo, np.roll(vol, 5, axis=2), probe=np.roll(probe, 5, axis=2))[0]
+    assert rel(Is, I) < 1e-12
+    # mirror y -> m' = -m mod ny; intensity mirrored in k_y
+    mirror = lambda a: np.roll(a[..., ::-1], 1, axis=-1)
+    Im = oracle_lib.forward(geo, mirror(vol), probe=mirror(probe))[0]
+    assert rel(Im, mirror(I)) < 1e-12
+    # but a shift along z with a fixed probe is not an invariant (the pin can fail)
+    Iz = oracle_lib.forward(geo, np.roll(vol, 5, axis=1), probe=probe)[0]
+    assert rel(Iz, I) > 1e-6
+
+
+# --------------------------------------------------------------------------
+# Kinematic (Born) limit of one weak slice
+# --------------------------------------------------------------------------
+def test_born_single_weak_slice(oracle_lib):
+    """t = 1 - i k Delta (delta - i beta) + O((k Delta |v|)^2): away from the
+    zero order Psi = F_u((-i k Delta delta - k Delta beta) phi0) for a plane wave."""
+    ny, nz, delta = 32, 64, 20.0
+    kd = K * delta
+    geo = oracle_lib.Geometry(ny, nz, 1, slice_nm=delta, alpha_i_deg=(0.0,))
+    rng = np.random.default_rng(4)
+    eps = 1e-4
+    v = (rng.uniform(0, 1, (1, nz, ny)) + 1j * rng.uniform(0, 0.3, (1, nz, ny))) * eps / kd
+    I, psi = oracle_lib.forward(geo, v, return_field=True)
+    born = np.fft.fft2(-1j * kd * v[0].real - kd * v[0].imag, norm="ortho")
+    mask = np.ones((nz, ny), bool)
+    mask[0, 0] = False
+    vmax = kd * np.abs(v).max()
+    assert rel(psi[0][mask], born[mask]) < 3 * vmax
+    # the opposite phase convention is far outside that band
+    wrong = np.fft.fft2(1j * kd * v[0].real - kd * v[0].imag, norm="ortho")
+    assert rel(psi[0][mask], wrong[mask]) > 0.1
+    # zero order: sqrt(N) * mean transmission
+    assert abs(psi[0][0, 0] - np.sqrt(nz * ny) * np.exp(-1j * kd * np.conj(v[0])).mean()) < 1e-12
+
+
+# --------------------------------------------------------------------------
+# Fresnel reflectivity of a flat Si substrate across the critical angle
+# --------------------------------------------------------------------------
+D_SI, B_SI = 7.6e-6, 1.75e-7
+
+
+def _reflectivity(oracle_lib, adeg, delta=20.0, dz=2.0, nz=1024, w0=50.0, h0=250.0):
+    a = np.deg2rad(adeg)
+    surf = nz // 2
+    ns = int(np.ceil((2.2 * h0 / np.tan(a) + 4 * w0 / np.sin(a)) / delta))
+    geo = oracle_lib.Geometry(1, nz, ns, slice_nm=delta, dz_nm=dz, alpha_i_deg=(adeg,))
+    one = np.zeros((1, nz, 1), np.complex128)
+    one[:, :surf, :] = D_SI + 1j * B_SI
+    one = ci.sponge(one, nz // 10, K * delta, strength=0.02 * delta / 20.0)
+    vol = np.broadcast_to(one, (ns, nz, 1))
+    probe = ci.gaussian_probe(1, nz, 2.0, dz, w0, z0_nm=surf * dz + h0, kz=-K * np.sin(a))[None]
+    I = oracle_lib.forward(geo, vol, probe=probe)
+    kz = 2 * np.pi * np.fft.fftfreq(nz, dz)
+    r_sim = I[0, kz > 0, 0].sum() / (np.abs(probe) ** 2).sum()
+    # closed form, weighted by the probe's angular spectrum (downward part)
+    A = np.abs(np.fft.fft(probe[0, :, 0])) ** 2
+    ap = -kz / K
+    m = ap > 0
+    q = np.sqrt(ap[m] ** 2 - 2 * D_SI + 2j * B_SI + 0j)
+    r = (ap[m] - q) / (ap[m] + q)
+    r_exp = (A[m] * np.abs(r) ** 2).sum() / A.sum()
+    return r_sim, r_exp
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("adeg", [0.15, 0.2, 0.25, 0.3, 0.4, 0.5])
+def test_fresnel_reflectivity(oracle_lib, adeg):
+    """Specular reflectivity r = (a - sqrt(a^2 - 2 delta + 2 i beta)) / (a + ...)
+    across alpha_c = sqrt(2 delta) ~ 0.223 deg (R falls from ~0.95 to ~0.003)."""
+    r_sim, r_exp = _reflectivity(oracle_lib, adeg)
+    assert abs(r_sim - r_exp) < 0.01, (r_sim, r_exp)
+
+
+@pytest.mark.slow
+def test_fresnel_reflectivity_small_angle(oracle_lib):
+    """0.1 deg needs a wider beam so that its angular spread stays well below alpha."""
+    r_sim, r_exp = _reflectivity(oracle_lib, 0.1, nz=2048, w0=100.0, h0=400.0)
+    assert abs(r_sim - r_exp) < 0.01, (r_sim, r_exp)
+
+
+def test_fresnel_total_reflection_needs_the_substrate(oracle_lib):
+    """Without delta in the substrate nothing comes back up."""
+    nz, dz, delta, adeg = 512, 2.0, 20.0, 0.2
+    a = np.deg2rad(adeg)
+    ns = int(2.2 * 200 / np.tan(a) / delta)
+    geo = oracle_lib.Geometry(1, nz, ns, slice_nm=delta, dz_nm=dz, alpha_i_deg=(adeg,))
+    probe = ci.gaussian_probe(1, nz, 2.0, dz, 50.0, z0_nm=nz // 2 * dz + 150, kz=-K * np.sin(a))[None]
+    one = np.zeros((1, nz, 1), np.complex128)
+    one[:, : nz // 2, :] = 1j * B_SI
+    vol = np.broadcast_to(ci.sponge(one, 48, K * delta, 0.02), (ns, nz, 1))
+    I = oracle_lib.forward(geo, vol, probe=probe)
+    kz = 2 * np.pi * np.fft.fftfreq(nz, dz)
+    assert I[0, kz > 0, 0].sum() / (np.abs(probe) ** 2).sum() < 1e-3
+
+
+# --------------------------------------------------------------------------
+# Slice-thickness convergence (Sec. 3: finer Delta changes little)
+# --------------------------------------------------------------------------
+def test_slice_thickness_convergence(oracle_lib):
+    ny, nz, length = 32, 64, 640.0
+    vol_coarse = ci.pillars_small(3, ny=ny, nz=nz, ns=8)
+    diffs = []
+    prev = None
+    for rep in (1, 2, 4, 8):
+        ns = 8 * rep
+        geo = oracle_lib.Geometry(ny, nz, ns, slice_nm=length / ns)
+        vol = np.repeat(vol_coarse, rep, axis=0)
+        I = oracle_lib.forward(geo, vol)[0]
+        if prev is not None:
+            diffs.append(rel(I, prev))
+        prev = I
+    # first-order splitting: successive changes shrink
+    assert diffs[1] < diffs[0] and diffs[2] < diffs[1]
+
+
+# --------------------------------------------------------------------------
+# Gradient: central finite differences and the transpose identity
+# --------------------------------------------------------------------------
+def _loss_only(oracle_lib, geo, vol, meas, s, probe):
+    I = oracle_lib.forward(geo, vol, probe=probe)
+    return float(((np.sqrt(s * I) - meas) ** 2).sum())
+
+
+def test_loss_matches_forward(oracle_lib):
+    ny, nz, ns = 16, 32, 6
+    geo = oracle_lib.Geometry(ny, nz, ns, alpha_i_deg=(0.3,))
+    vol = ci.random_volume(2, ny, nz, ns, scale=40).astype(np.complex128)
+    meas = np.random.default_rng(2).uniform(0.5, 2.0, (1, nz, ny))
+    L, g, I = oracle_lib.loss_grad(geo, vol, meas, 0.7, return_intensity=True)
+    assert abs(L - _loss_only(oracle_lib, geo, vol, meas, 0.7, None)) < 1e-10 * L
+    assert rel(I, oracle_lib.forward(geo, vol)) < 1e-14
+
+
+def test_gradient_central_differences(oracle_lib):
+    """dL/ddelta and dL/dbeta on a 16x16x8 sub-volume of a 32x32x16 grid."""
+    ny, nz, ns = 32, 32, 16
+    geo = oracle_lib.Geometry(ny, nz, ns, alpha_i_deg=(0.3,))
+    vol = ci.random_volume(11, ny, nz, ns, scale=40).astype(np.complex128)
+    probe = ci.random_probe(11, 1, ny, nz).astype(np.complex128)
+    I0 = oracle_lib.forward(geo, vol, probe=probe)
+    meas = np.sqrt(I0) * np.random.default_rng(3).uniform(0.5, 1.5, I0.shape)
+    s = 1.3
+    L, g = oracle_lib.loss_grad(geo, vol, meas, s, probe=probe)
+    h = 1e-4 * np.abs(vol).max()
+    rng = np.random.default_rng(5)
+    # every voxel of the sub-volume for delta would be 2048 x 4 evaluations;
+    # a seeded random sample of 96 voxels keeps the CPU suite short
+    idx = [(int(rng.integers(4, 12)), int(rng.integers(8, 24)), int(rng.integers(8, 24)))
+           for _ in range(96)]
+    fd, an = [], []
+    for (x, z, y) in idx:
+        for part, unit in ((0, 1.0), (1, 1j)):
+            vp = vol.copy(); vp[x, z, y] += h * unit
+            vm = vol.copy(); vm[x, z, y] -= h * unit
+            d = (_loss_only(oracle_lib, geo, vp, meas, s, probe)
+                 - _loss_only(oracle_lib, geo, vm, meas, s, probe)) / (2 * h)
+            fd.append(d)
+            an.append(g[x, z, y].real if part == 0 else g[x, z, y].imag)
+    fd, an = np.array(fd), np.array(an)
+    assert np.linalg.norm(fd - an) / np.linalg.norm(fd) < 1e-6
+
+
+def test_adjoint_transpose_identity(oracle_lib):
+    """<g, J w>_R = <J^T g, w> with J w the directional derivative of Psi."""
+    ny, nz, ns = 16, 16, 10
+    geo = oracle_lib.Geometry(ny, nz, ns, alpha_i_deg=(0.25, 0.35))
+    vol = ci.random_volume(21, ny, nz, ns, scale=40).astype(np.complex128)
+    rng = np.random.default_rng(21)
+    w = rng.normal(size=vol.shape) + 1j * rng.normal(size=vol.shape)
+    gpsi = rng.normal(size=(2, nz, ny)) + 1j * rng.normal(size=(2, nz, ny))
+    h = 1e-3 * np.abs(vol).max() / np.abs(w).max()
+    _, pp = oracle_lib.forward(geo, vol + h * w, return_field=True)
+    _, pm = oracle_lib.forward(geo, vol - h * w, return_field=True)
+    jw = (pp - pm) / (2 * h)
+    lhs = float(np.real(np.vdot(gpsi, jw)))
+    grad = oracle_lib.adjoint(geo, vol, gpsi)
+    rhs = float((grad.real * w.real + grad.imag * w.imag).sum())
+    assert abs(lhs - rhs) < 1e-6 * abs(lhs)
+
+
+def test_loss_seed_zero_amplitude(oracle_lib):
+    """Where the model amplitude vanishes the seed is 0 (the sqrt is singular)."""
+    ny, nz, ns = 8, 8, 2
+    geo = oracle_lib.Geometry(ny, nz, ns)
+    probe = np.zeros((1, nz, ny), np.complex128)
+    L, g = oracle_lib.loss_grad(geo, np.zeros((ns, nz, ny)), np.ones((1, nz, ny)), 1.0, probe=probe)
+    assert L == pytest.approx(nz * ny)
+    assert np.all(g == 0)

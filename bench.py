@@ -1,0 +1,378 @@
+#!/usr/bin/env python
+"""Benchmark of the multislice forward model + adjoint (one loss-gradient
+evaluation) on synthetic CSSI volumes.
+
+Workload (one step): 512 x 512 (y, z) grid at 2 nm, 1024 slices of 20 nm,
+9 incidence angles 0.10-0.50 deg through one volume, Si substrate with 50 Au
+pillars/lines, amplitude loss against Poisson targets (1e6 counts per angle),
+gradient on delta/beta with checkpoints every 32 slices.
+
+Metric: voxel-slice-steps/s, one unit = one grid point of one wavefield taken
+through one slice forward AND back (ny*nz*ns*nw units per step).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+Under torchrun each rank runs its own volume (seed = rank): weak scaling, no
+data-path collective; the JSON line (rank 0) reports the whole-job rate.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+NY = NZ = 512
+NS = 1024
+NW = 9
+DZ = DY = 2.0
+SLICE = 20.0
+LAM = 0.155
+COUNTS = 1e6
+CKPT = 32
+METRIC = "multislice voxel-steps/s fwd+adjoint"
+UNIT = "voxel-slice-steps/s"
+
+
+def config(nw=NW, ns=NS):
+    return {
+        "workload": "512x512 grid (2 nm), %d slices of 20 nm, %d incidence angles 0.10-0.50 deg, "
+                    "Si + 50 Au pillars/lines, loss + gradient (checkpoint every %d)" % (ns, nw, CKPT),
+        "grid": [NY, NZ], "slices": ns, "angles": nw, "wavelength_nm": LAM,
+        "l2": "inputs larger than L2: the 2 GiB volume and 2 GiB transmission stream from HBM every pass",
+    }
+
+
+def angles(nw=NW):
+    return np.linspace(0.1, 0.5, nw)
+
+
+# ---------------------------------------------------------------------------
+# clocks sampler (nvidia-smi during the timed region)
+# ---------------------------------------------------------------------------
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.idx = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "50"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.12)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
+                "power_w_max": max(power) if power else None, "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------
+# algorithmic work per unit (FFT flops counted as 5 N log2 N per length-N
+# complex transform, complex multiply 6, per grid point per slice)
+# ---------------------------------------------------------------------------
+def flops_per_unit(kernel, ny=NY, nz=NZ):
+    fft_pair = 2 * 5 * (np.log2(ny) + np.log2(nz))  # forward + inverse along y and z
+    if kernel == "k_fwd":
+        return 6 + fft_pair + 12                   # transmission, FFTs, P_y and P_z
+    if kernel == "k_adj":
+        return 6 + fft_pair + 12 + 8               # + gradient a conj(g) scaled
+    if kernel == "k_last":
+        return 6 + 5 * (np.log2(ny) + np.log2(nz)) * 2 + 20
+    return 0.0
+
+
+def fp32_peak_tflops(sms, mhz):
+    return sms * 128 * 2 * mhz * 1e6 / 1e12
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def traffic_record(kernel):
+    """DRAM bytes per unit from a committed ncu summary, if the kernel source is unchanged."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    src = os.path.join(ROOT, "paper_2212_01253_gb300", "csrc", "mslice.cu")
+    try:
+        rec = json.load(open(path))
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        if rec.get("source_sha256_16") != h:
+            return None
+        return rec["kernels"].get(kernel, {}).get("dram_bytes_per_unit")
+    except (OSError, ValueError, KeyError):
+        return None
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle leg
+# ---------------------------------------------------------------------------
+def oracle_rate(ns_sample, reps=1):
+    """Oracle loss+gradient on 512^2 x ns_sample slices x 1 angle; units/s."""
+    import cssi_inputs as ci
+    import oracle
+
+    geo = oracle.Geometry(NY, NZ, ns_sample, LAM, SLICE, DY, DZ, alpha_i_deg=(0.3,))
+    vol = ci.pillars_large(0, ns=ns_sample)
+    meas = np.ones((1, NZ, NY), np.float64)
+    times = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        oracle.loss_grad(geo, vol, meas, 1.0)
+        times.append(time.perf_counter() - t0)
+    units = NY * NZ * ns_sample
+    return units, times, oracle.num_threads()
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    ns_sample = 16
+    units, times, cores = oracle_rate(ns_sample, reps=args.warmup + args.steps)
+    timed = times[args.warmup:]
+    per_step = sum(timed) / len(timed)
+    value = units / per_step
+    sample = "512x512 grid, %d of 1024 slices, 1 of 9 angles per step (FP64 oracle loss+gradient)" % ns_sample
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config(),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU leg
+# ---------------------------------------------------------------------------
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    import cssi_inputs as ci
+    from paper_2212_01253_gb300 import binding as B
+    from paper_2212_01253_gb300 import build as cuda_build
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0 or not os.path.exists(cuda_build.LIB):
+        cuda_build.build()
+    if world > 1:
+        dist.barrier()
+    dev = torch.device("cuda", local)
+    nw, ns = args.angles, args.slices
+    p = B.make_params(NY, NZ, ns, angles(nw), LAM, SLICE, DY, DZ, CKPT)
+
+    # inputs: volume (seed = rank) and Poisson targets of a ground-truth volume
+    vol_h = ci.pillars_large(rank, ns=ns)
+    truth_h = ci.pillars_large(1000 + rank, ns=ns)
+    vol = torch.from_numpy(vol_h).to(dev)
+    ws = torch.empty(B.mslice_workspace_size(p, B.MSLICE_OP_LOSS_GRAD), dtype=torch.uint8, device=dev)
+    inten = torch.empty((nw, NZ, NY), dtype=torch.float32, device=dev)
+    B.mslice_forward(p, torch.from_numpy(truth_h).to(dev), None, inten, None, ws)
+    I_gt = inten.cpu().numpy()
+    meas_h = np.empty_like(I_gt, dtype=np.float32)
+    scales = []
+    for w in range(nw):
+        m, s = ci.poisson_target(I_gt[w], COUNTS, seed=rank * 100 + w)
+        meas_h[w] = m
+        scales.append(s)
+    # one scale for all angles: the flux is the same, so use their mean
+    s = float(np.mean(scales))
+    meas = torch.from_numpy(meas_h).to(dev)
+    loss = torch.zeros(1, dtype=torch.float64, device=dev)
+    grad = torch.empty_like(vol)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        B.mslice_loss_grad(p, vol, None, meas, s, loss, grad, None, ws)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if B.mslice_status(ws) != 0:
+        raise RuntimeError("device-side wait timed out during warm-up")
+    if world > 1:
+        dist.barrier()
+    clocks = Clocks(local)
+    clocks.start()
+    time.sleep(0.1)
+    B.mslice_profile_enable(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    prof = B.mslice_profile_read()
+    B.mslice_profile_enable(False)
+    clk = clocks.stop()
+    if world > 1:
+        dist.barrier()
+    ms = e0.elapsed_time(e1) / args.steps
+    if B.mslice_status(ws) != 0:
+        raise RuntimeError("device-side wait timed out in the timed region")
+    ms_t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+    units_step = NY * NZ * ns * nw
+    value = world * units_step / (ms_max / 1e3)
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        vol_pin = torch.from_numpy(vol_h).pin_memory()
+        meas_pin = torch.from_numpy(meas_h).pin_memory()
+        grad_pin = torch.empty(grad.shape, dtype=grad.dtype).pin_memory()
+        loss_pin = torch.empty(1, dtype=torch.float64).pin_memory()
+
+        def e2e_step():
+            vol.copy_(vol_pin, non_blocking=True)
+            meas.copy_(meas_pin, non_blocking=True)
+            step()
+            grad_pin.copy_(grad, non_blocking=True)
+            loss_pin.copy_(loss, non_blocking=True)
+
+        for _ in range(2):
+            e2e_step()
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(args.steps):
+            e2e_step()
+        f1.record(stream)
+        torch.cuda.synchronize()
+        ems = torch.tensor([f0.elapsed_time(f1) / args.steps], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(ems, op=dist.ReduceOp.MAX)
+        e2e = {"value": world * units_step / (float(ems.item()) / 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": vol_pin.numel() * 8 + meas_pin.numel() * 4,
+               "d2h_bytes_per_step": grad_pin.numel() * 8 + 8}
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+
+    # roofline of the dominant kernel
+    peaks = measured_peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    dom = max(prof.items(), key=lambda kv: kv[1][1])
+    name, (launches, total_ms, units) = dom
+    flops = flops_per_unit(name) * units / launches
+    launch_s = total_ms / launches / 1e3
+    achieved = flops / launch_s / 1e12
+    peak = fp32_peak_tflops(sms, mhz)
+    tb = traffic_record(name)
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None if tb is None else tb * units / launches,
+                "kernel": name, "launches": launches, "avg_launch_ms": total_ms / launches,
+                "peak_basis": "FP32 FMA rate: %d SMs x 128 lanes x 2 flop x %.0f MHz (of measured "
+                              "sm_max_mhz)" % (sms, mhz),
+                "flops_per_unit": flops_per_unit(name)}
+    kernels = {k: {"launches": v[0], "total_ms": v[1], "units": v[2]} for k, v in prof.items()}
+    gpu_launches = sum(v[0] for v in prof.values())
+
+    cpu = None
+    if not args.no_cpu_baseline and world == 1 or (not args.no_cpu_baseline and rank == 0):
+        ns_sample = args.cpu_slices
+        u, times, cores = oracle_rate(ns_sample, reps=1)
+        cpu = {"value": u / times[0], "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": "512x512 grid, %d of 1024 slices, 1 of 9 angles (FP64 oracle loss+gradient, "
+                         "%.1f s)" % (ns_sample, times[0])}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config(nw, ns),
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+            "gpu_launches": gpu_launches, "kernels": kernels, "loss": float(loss.item())}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--angles", type=int, default=NW)
+    ap.add_argument("--slices", type=int, default=NS)
+    ap.add_argument("--cpu-slices", type=int, default=96)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("at least 3 warm-up steps")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

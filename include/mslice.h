@@ -1,0 +1,177 @@
+/*
+ * mslice.h -- C ABI of libmslice: the reflection-geometry multislice forward
+ * model of Coherent Surface Scattering Imaging (arxiv 2212.01253) and its
+ * gradient, on one NVIDIA GB300 (sm_103a).
+ *
+ * Physics (paper notation):
+ *   Eq. 1 (Sec. 1)  one slice of thickness Delta:
+ *       phi(Z0+Delta) = F^-1{ exp(-i Delta (kX^2+kY^2)/2k) F{ exp((k/2i) int (1-n^2) dZ) phi(Z0) } }
+ *     implemented with n = 1 - delta + i beta, the linearised 1-n^2 ~ 2(delta - i beta),
+ *     one voxel per slice, so the transmission is t = exp(-i k Delta (delta - i beta)),
+ *     and without the global phase exp(i k Delta).
+ *   Fig. 1a: the exit wave of the last slice is Fourier transformed and squared:
+ *     I = |Psi|^2, Psi = F_unitary(t_Ns * phi_{Ns-1}) (the last propagation and the
+ *     free propagation to the detector are pure Fourier phases and are skipped).
+ *   Eq. 4 (Sec. 4.1): the loss is the squared error of amplitudes; this library
+ *     sums it (no 1/N): L = sum (sqrt(s I) - m)^2, m = sqrt(I_meas).
+ *   Sec. 2, Eq. 2-3: the incidence angle alpha_i is applied by tilting the probe
+ *     toward the substrate, phi_0(y, z) = exp(-i k sin(alpha_i) z), instead of
+ *     rotating the volume (paraxially equivalent); psi (yaw) must be 0.
+ *
+ * Axes and layouts (all arrays row-major, last index fastest):
+ *   x  = slice index along the beam, ns slices of thickness slice_nm (Delta);
+ *   z  = surface normal, nz pixels of dz_nm, z index 0 = bottom (substrate side);
+ *   y  = in-plane transverse axis, ny pixels of dy_nm.
+ *   A complex value is two floats (re, im).  The volume holds delta + i*beta.
+ *   Frequencies: k_y = 2 pi fftfreq(ny, dy), k_z = 2 pi fftfreq(nz, dz); forward DFT
+ *   kernel exp(-i ...); detector images are in natural (unshifted) FFT order.
+ *
+ * Memory and streams:
+ *   Every pointer argument except `p` is a DEVICE pointer owned by the caller.
+ *   The library allocates no device memory: scratch lives in the caller's
+ *   workspace `ws` (size from mslice_workspace_size(), 256-byte aligned; its
+ *   contents need no initialisation and are clobbered).  All work is enqueued on
+ *   `stream` (a cudaStream_t, NULL = legacy default stream) and is asynchronous;
+ *   outputs are valid once the stream reaches them.  Outputs must not alias
+ *   inputs or the workspace.  Calls sharing one workspace must not overlap.
+ *
+ * Errors: functions return MSLICE_OK (0) or a negative MSLICE_E* code; they never
+ * abort or trap.  Device-side waits are bounded: a wait that runs out marks the
+ * workspace's status word; mslice_status() reports it as MSLICE_ETIMEDOUT.
+ */
+#ifndef MSLICE_H
+#define MSLICE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MSLICE_MAX_ANGLES 64
+#define MSLICE_MAX_N 1024
+
+/* return codes */
+#define MSLICE_OK 0
+#define MSLICE_EINVAL (-1)        /* bad size, pointer, alignment or parameter */
+#define MSLICE_EUNSUPPORTED (-2)  /* valid request outside what is built (psi != 0, ...) */
+#define MSLICE_ELAUNCH (-3)       /* a CUDA launch or runtime call failed */
+#define MSLICE_ETIMEDOUT (-4)     /* a bounded device-side wait ran out */
+#define MSLICE_EWORKSPACE (-5)    /* workspace smaller than mslice_workspace_size() */
+
+/* ops for mslice_workspace_size */
+#define MSLICE_OP_FORWARD 0
+#define MSLICE_OP_ADJOINT 1
+#define MSLICE_OP_LOSS_GRAD 2
+
+/* flags */
+#define MSLICE_EXIT_WAVE 1u  /* forward: field_out = phi_Ns (after the full last
+                                propagation) and intensity = |phi_Ns|^2 instead of
+                                the far field; used for near-field checks */
+
+typedef struct mslice_params {
+    double wavelength_nm;      /* lambda; k = 2 pi / lambda is formed in FP64 */
+    double slice_nm;           /* Delta: slice thickness along the beam */
+    double dy_nm;              /* pixel size along y */
+    double dz_nm;              /* pixel size along z (surface normal) */
+    int32_t ny, nz;            /* powers of two in [1, MSLICE_MAX_N] */
+    int32_t ns;                /* number of slices, >= 1 */
+    int32_t nw;                /* number of wavefields (incidence angles), 1..MSLICE_MAX_ANGLES */
+    double alpha_i_rad[MSLICE_MAX_ANGLES]; /* incidence angle of each wavefield */
+    double psi_rad;            /* in-plane (yaw) angle: must be 0 */
+    int32_t checkpoint_every;  /* adjoint segment length in slices; <= 0 means 32 */
+    uint32_t flags;            /* MSLICE_EXIT_WAVE */
+} mslice_params;
+
+/* Bytes of workspace needed by `op` (MSLICE_OP_*) for these parameters;
+ * 0 if the parameters are invalid. */
+size_t mslice_workspace_size(const mslice_params *p, int op);
+
+/* Forward model (Eq. 1 slice loop, then the far field of Fig. 1a).
+ *   vol        [ns][nz][ny] complex: delta + i beta of each voxel (read only)
+ *   probe      NULL for the tilted unit plane wave exp(-i k sin(alpha_w) z_l),
+ *              or [nw][nz][ny] complex user probe phi_0 (Sec. 5: any probe shape)
+ *   intensity  [nw][nz][ny] float: I = |Psi|^2 (may be NULL)
+ *   field_out  NULL or [nw][nz][ny] complex: Psi (or phi_Ns with MSLICE_EXIT_WAVE) */
+int mslice_forward(const mslice_params *p, const float *vol, const float *probe,
+                   float *intensity, float *field_out, void *ws, size_t ws_bytes,
+                   void *stream);
+
+/* Gradient of a real loss through the forward model, for a given detector
+ * gradient (replaces the autograd backward of Sec. 3-4).
+ *   g_psi      [nw][nz][ny] complex: dL/dRe(Psi) + i dL/dIm(Psi)
+ *   grad_vol   [ns][nz][ny] complex out: dL/ddelta + i dL/dbeta, summed over
+ *              wavefields.  Slice checkpoints every checkpoint_every slices are
+ *              kept in the workspace and segments are recomputed. */
+int mslice_adjoint(const mslice_params *p, const float *vol, const float *probe,
+                   const float *g_psi, float *grad_vol, void *ws, size_t ws_bytes,
+                   void *stream);
+
+/* Amplitude loss of Eq. 4 (summed) and its gradient on delta/beta.
+ *   meas_amp   [nw][nz][ny] float: m = sqrt(I_meas)
+ *   scale      s > 0: model intensity scale (photon flux)
+ *   loss_out   device double[1]: L = sum_w sum_px (sqrt(s I) - m)^2 (FP64 sum)
+ *   grad_vol   [ns][nz][ny] complex out, as for mslice_adjoint
+ *   intensity  NULL or [nw][nz][ny] float out: I of the model */
+int mslice_loss_grad(const mslice_params *p, const float *vol, const float *probe,
+                     const float *meas_amp, float scale, double *loss_out, float *grad_vol,
+                     float *intensity, void *ws, size_t ws_bytes, void *stream);
+
+/* The FP64-built constant arrays ("C" of Fig. 1), rounded to float:
+ *   py [ny] complex: exp(-i Delta k_y^2 / 2k);  pz [nz] complex: exp(-i Delta k_z^2 / 2k)
+ *   probe_z [nw][nz] complex: exp(-i k sin(alpha_w) z_l) (default probe, one value per row)
+ * Any output may be NULL.  Uses the workspace of MSLICE_OP_FORWARD. */
+int mslice_plan_tables(const mslice_params *p, float *py, float *pz, float *probe_z,
+                       void *ws, size_t ws_bytes, void *stream);
+
+/* Transmission of every voxel (Eq. 1 first factor): t = exp(-i k Delta (delta - i beta)),
+ * phase arguments k*Delta*delta and k*Delta*beta formed in FP64.
+ *   vol [ns][nz][ny] complex in;  t_out [ns][nz][ny] complex out.  No workspace. */
+int mslice_transmission(const mslice_params *p, const float *vol, float *t_out, void *stream);
+
+/* Vector-Jacobian product of the detector intensity I = |Psi|^2 (Fig. 1a):
+ * g_psi[i] = 2 dI[i] Psi[i], the detector gradient (dL/dRe + i dL/dIm) that
+ * mslice_adjoint() takes when the loss is a function of I.  n complex
+ * elements; psi, g_psi complex, dI float; no workspace. */
+int mslice_intensity_vjp(const float *psi, const float *dI, float *g_psi, size_t n, void *stream);
+
+/* Waits for `stream`, then reads the workspace status word: MSLICE_OK, or
+ * MSLICE_ETIMEDOUT if a device-side wait of an earlier call ran out. */
+int mslice_status(const void *ws, void *stream);
+
+/* Test hook for the bounded grid wait: launches `nblocks` cooperating blocks
+ * that wait for nblocks + withhold arrivals with a limit of timeout_ns.  With
+ * withhold > 0 nobody ever completes the wait, every block gives up after the
+ * limit and the status word records MSLICE_ETIMEDOUT.  ws >= 4096 bytes. */
+int mslice_debug_wait(int nblocks, int withhold, long long timeout_ns, void *ws,
+                      size_t ws_bytes, void *stream);
+
+/* Per-kernel timing (tracing).  While enabled, every kernel launch of the
+ * library is bracketed by a CUDA event pair recorded on the launching stream;
+ * mslice_profile_read() waits for the recorded events and returns, per kernel
+ * name, the launch count, the summed device time and the summed work units
+ * (one unit = one grid point of one wavefield advanced through one slice).
+ * Enabling resets the counters.  Not thread-safe; host-side bookkeeping only. */
+typedef struct mslice_kernel_time {
+    char name[32];
+    int32_t launches;
+    double total_ms;
+    double units;
+} mslice_kernel_time;
+
+int mslice_profile_enable(int on);
+/* Fills up to max_entries records; returns the number filled or a negative code. */
+int mslice_profile_read(mslice_kernel_time *out, int max_entries);
+
+/* Text of the last failing CUDA runtime call of this thread ("" if none);
+ * explains an MSLICE_ELAUNCH. */
+const char *mslice_last_cuda_error(void);
+
+/* Static text for a return code. */
+const char *mslice_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MSLICE_H */

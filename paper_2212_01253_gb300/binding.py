@@ -1,0 +1,242 @@
+"""Python binding of libmslice (include/mslice.h): argument marshalling only.
+
+Every function has the name of the C entry point it calls.  Arrays are torch
+tensors on the current CUDA device (complex arrays as complex64); the call is
+enqueued on torch's current stream.  All arithmetic runs in the library's
+CUDA kernels; if the library is missing, loading fails with an error (there
+is no CPU fallback).
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import threading
+
+import torch
+
+from . import build as _build
+
+MSLICE_MAX_ANGLES = 64
+MSLICE_OP_FORWARD, MSLICE_OP_ADJOINT, MSLICE_OP_LOSS_GRAD = 0, 1, 2
+MSLICE_EXIT_WAVE = 1
+ERRORS = {-1: "MSLICE_EINVAL", -2: "MSLICE_EUNSUPPORTED", -3: "MSLICE_ELAUNCH",
+          -4: "MSLICE_ETIMEDOUT", -5: "MSLICE_EWORKSPACE"}
+
+
+class MsliceError(RuntimeError):
+    def __init__(self, code, what):
+        self.code = code
+        msg = "%s failed: %s (%s)" % (what, ERRORS.get(code, code), mslice_strerror(code))
+        if code == -3:
+            msg += ": " + _load().mslice_last_cuda_error().decode()
+        super().__init__(msg)
+
+
+class mslice_params(ctypes.Structure):
+    _fields_ = [
+        ("wavelength_nm", ctypes.c_double),
+        ("slice_nm", ctypes.c_double),
+        ("dy_nm", ctypes.c_double),
+        ("dz_nm", ctypes.c_double),
+        ("ny", ctypes.c_int32),
+        ("nz", ctypes.c_int32),
+        ("ns", ctypes.c_int32),
+        ("nw", ctypes.c_int32),
+        ("alpha_i_rad", ctypes.c_double * MSLICE_MAX_ANGLES),
+        ("psi_rad", ctypes.c_double),
+        ("checkpoint_every", ctypes.c_int32),
+        ("flags", ctypes.c_uint32),
+    ]
+
+
+def make_params(ny, nz, ns, alpha_i_deg=(0.3,), wavelength_nm=0.155, slice_nm=20.0,
+                dy_nm=2.0, dz_nm=2.0, checkpoint_every=32, flags=0, psi_rad=0.0):
+    """mslice_params from plain numbers (angles in degrees)."""
+    alphas = [math.radians(float(a)) for a in (alpha_i_deg if hasattr(alpha_i_deg, "__len__")
+                                               else [alpha_i_deg])]
+    if not 1 <= len(alphas) <= MSLICE_MAX_ANGLES:
+        raise ValueError("1..%d incidence angles" % MSLICE_MAX_ANGLES)
+    p = mslice_params()
+    p.wavelength_nm, p.slice_nm, p.dy_nm, p.dz_nm = wavelength_nm, slice_nm, dy_nm, dz_nm
+    p.ny, p.nz, p.ns, p.nw = int(ny), int(nz), int(ns), len(alphas)
+    for i, a in enumerate(alphas):
+        p.alpha_i_rad[i] = a
+    p.psi_rad = psi_rad
+    p.checkpoint_every = int(checkpoint_every)
+    p.flags = int(flags)
+    return p
+
+
+class mslice_kernel_time(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int32),
+                ("total_ms", ctypes.c_double), ("units", ctypes.c_double)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(_build.LIB):
+                raise RuntimeError("libmslice.so is not built (%s); run "
+                                   "paper_2212_01253_gb300.build.build()" % _build.LIB)
+            lib = ctypes.CDLL(_build.LIB)
+            P, vp, sz = ctypes.POINTER(mslice_params), ctypes.c_void_p, ctypes.c_size_t
+            sig = {
+                "mslice_workspace_size": ([P, ctypes.c_int], sz),
+                "mslice_forward": ([P, vp, vp, vp, vp, vp, sz, vp], ctypes.c_int),
+                "mslice_adjoint": ([P, vp, vp, vp, vp, vp, sz, vp], ctypes.c_int),
+                "mslice_loss_grad": ([P, vp, vp, vp, ctypes.c_float, vp, vp, vp, vp, sz, vp],
+                                     ctypes.c_int),
+                "mslice_plan_tables": ([P, vp, vp, vp, vp, sz, vp], ctypes.c_int),
+                "mslice_transmission": ([P, vp, vp, vp], ctypes.c_int),
+                "mslice_status": ([vp, vp], ctypes.c_int),
+                "mslice_intensity_vjp": ([vp, vp, vp, sz, vp], ctypes.c_int),
+                "mslice_debug_wait": ([ctypes.c_int, ctypes.c_int, ctypes.c_longlong, vp, sz, vp],
+                                      ctypes.c_int),
+                "mslice_strerror": ([ctypes.c_int], ctypes.c_char_p),
+                "mslice_last_cuda_error": ([], ctypes.c_char_p),
+                "mslice_profile_enable": ([ctypes.c_int], ctypes.c_int),
+                "mslice_profile_read": ([ctypes.POINTER(mslice_kernel_time), ctypes.c_int],
+                                        ctypes.c_int),
+            }
+            for name, (args, res) in sig.items():
+                f = getattr(lib, name)
+                f.argtypes, f.restype = args, res
+            _lib = lib
+    return _lib
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t, dtype=None, numel=None, what="tensor"):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("%s must be a CUDA tensor" % what)
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % what)
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError("%s must be %s, got %s" % (what, dtype, t.dtype))
+    if numel is not None and t.numel() != numel:
+        raise ValueError("%s must have %d elements, got %d" % (what, numel, t.numel()))
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _check(rc, what):
+    if rc != 0:
+        raise MsliceError(rc, what)
+
+
+def mslice_strerror(code: int) -> str:
+    return _load().mslice_strerror(int(code)).decode()
+
+
+def mslice_workspace_size(p: mslice_params, op: int) -> int:
+    n = _load().mslice_workspace_size(ctypes.byref(p), int(op))
+    if n == 0:
+        raise MsliceError(-1, "mslice_workspace_size")
+    return int(n)
+
+
+def workspace(p: mslice_params, op: int, device=None) -> torch.Tensor:
+    """A workspace tensor of mslice_workspace_size(p, op) bytes."""
+    return torch.empty(mslice_workspace_size(p, op), dtype=torch.uint8,
+                       device=device or torch.device("cuda"))
+
+
+def _sizes(p):
+    npx = p.ny * p.nz
+    return p.ns * npx, p.nw * npx
+
+
+def mslice_forward(p, vol, probe, intensity, field_out, ws, stream=None):
+    nvol, nfield = _sizes(p)
+    _check(_load().mslice_forward(
+        ctypes.byref(p), _ptr(vol, torch.complex64, nvol, "vol"),
+        _ptr(probe, torch.complex64, nfield, "probe"),
+        _ptr(intensity, torch.float32, nfield, "intensity"),
+        _ptr(field_out, torch.complex64, nfield, "field_out"),
+        _ptr(ws, torch.uint8, None, "ws"), ws.numel(), _stream(stream)), "mslice_forward")
+
+
+def mslice_adjoint(p, vol, probe, g_psi, grad_vol, ws, stream=None):
+    nvol, nfield = _sizes(p)
+    _check(_load().mslice_adjoint(
+        ctypes.byref(p), _ptr(vol, torch.complex64, nvol, "vol"),
+        _ptr(probe, torch.complex64, nfield, "probe"),
+        _ptr(g_psi, torch.complex64, nfield, "g_psi"),
+        _ptr(grad_vol, torch.complex64, nvol, "grad_vol"),
+        _ptr(ws, torch.uint8, None, "ws"), ws.numel(), _stream(stream)), "mslice_adjoint")
+
+
+def mslice_loss_grad(p, vol, probe, meas_amp, scale, loss_out, grad_vol, intensity, ws, stream=None):
+    nvol, nfield = _sizes(p)
+    _check(_load().mslice_loss_grad(
+        ctypes.byref(p), _ptr(vol, torch.complex64, nvol, "vol"),
+        _ptr(probe, torch.complex64, nfield, "probe"),
+        _ptr(meas_amp, torch.float32, nfield, "meas_amp"), ctypes.c_float(scale),
+        _ptr(loss_out, torch.float64, 1, "loss_out"),
+        _ptr(grad_vol, torch.complex64, nvol, "grad_vol"),
+        _ptr(intensity, torch.float32, nfield, "intensity"),
+        _ptr(ws, torch.uint8, None, "ws"), ws.numel(), _stream(stream)), "mslice_loss_grad")
+
+
+def mslice_plan_tables(p, py, pz, probe_z, ws, stream=None):
+    _check(_load().mslice_plan_tables(
+        ctypes.byref(p), _ptr(py, torch.complex64, p.ny, "py"),
+        _ptr(pz, torch.complex64, p.nz, "pz"),
+        _ptr(probe_z, torch.complex64, p.nw * p.nz, "probe_z"),
+        _ptr(ws, torch.uint8, None, "ws"), ws.numel(), _stream(stream)), "mslice_plan_tables")
+
+
+def mslice_transmission(p, vol, t_out, stream=None):
+    nvol, _ = _sizes(p)
+    _check(_load().mslice_transmission(
+        ctypes.byref(p), _ptr(vol, torch.complex64, nvol, "vol"),
+        _ptr(t_out, torch.complex64, nvol, "t_out"), _stream(stream)), "mslice_transmission")
+
+
+def mslice_intensity_vjp(psi, dI, g_psi, stream=None):
+    n = psi.numel()
+    _check(_load().mslice_intensity_vjp(
+        _ptr(psi, torch.complex64, n, "psi"), _ptr(dI, torch.float32, n, "dI"),
+        _ptr(g_psi, torch.complex64, n, "g_psi"), n, _stream(stream)), "mslice_intensity_vjp")
+
+
+def mslice_status(ws, stream=None) -> int:
+    """0, or a negative code (-4 = MSLICE_ETIMEDOUT) recorded by a device-side wait."""
+    return int(_load().mslice_status(_ptr(ws, torch.uint8, None, "ws"), _stream(stream)))
+
+
+def mslice_debug_wait(nblocks, withhold, timeout_ns, ws, stream=None):
+    _check(_load().mslice_debug_wait(int(nblocks), int(withhold), int(timeout_ns),
+                                     _ptr(ws, torch.uint8, None, "ws"), ws.numel(),
+                                     _stream(stream)), "mslice_debug_wait")
+
+
+def mslice_profile_enable(on: bool = True):
+    """Start (and reset) or stop the per-launch event timing of the library."""
+    _check(_load().mslice_profile_enable(int(bool(on))), "mslice_profile_enable")
+
+
+def mslice_profile_read():
+    """{kernel name: (launches, total_ms, units)} since the last enable."""
+    buf = (mslice_kernel_time * 16)()
+    n = _load().mslice_profile_read(buf, 16)
+    if n < 0:
+        raise MsliceError(n, "mslice_profile_read")
+    return {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].total_ms), float(buf[i].units))
+            for i in range(n)}

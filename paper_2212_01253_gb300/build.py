@@ -1,19 +1,27 @@
-"""Builds libmslice.so (sm_103a) in-tree with nvcc."""
+"""Builds libmslice.so (sm_103a) in-tree with nvcc.
+
+The slice-loop kernels are specialised per (ny, nz) and compiled in one
+translation unit per row length, in parallel; the host/C-ABI unit is compiled
+alongside, and the objects are linked into one shared library.
+"""
 from __future__ import annotations
 
+import concurrent.futures as cf
+import glob
 import os
 import shutil
 import subprocess
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
-SRC = os.path.join(HERE, "csrc", "mslice.cu")
+CSRC = os.path.join(HERE, "csrc")
 HEADER = os.path.join(ROOT, "include", "mslice.h")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD_DIR, "libmslice.so")
+ROW_LENGTHS = (64, 128, 256, 512, 1024)
 
-NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
-              "-Xcompiler", "-fPIC", "-shared"]
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+CFLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC"]
 
 
 def nvcc() -> str:
@@ -23,23 +31,53 @@ def nvcc() -> str:
     raise RuntimeError("nvcc not found: the CUDA toolkit is required to build libmslice")
 
 
+def _sources():
+    return sorted(glob.glob(os.path.join(CSRC, "*.cu")) + glob.glob(os.path.join(CSRC, "*.cuh"))
+                  + glob.glob(os.path.join(CSRC, "*.h")) + [HEADER, os.path.abspath(__file__)])
+
+
 def up_to_date() -> bool:
     if not os.path.exists(LIB):
         return False
     t = os.path.getmtime(LIB)
-    return all(os.path.getmtime(f) <= t for f in (SRC, HEADER, __file__))
+    return all(os.path.getmtime(f) <= t for f in _sources())
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
+def _units():
+    inc = ["-I", os.path.join(ROOT, "include"), "-I", CSRC]
+    units = [(os.path.join(CSRC, "mslice.cu"), os.path.join(BUILD_DIR, "mslice.o"), inc)]
+    for ny in ROW_LENGTHS:
+        units.append((os.path.join(CSRC, "mslice_inst.cu"), os.path.join(BUILD_DIR, "inst_ny%d.o" % ny),
+                      inc + ["-DMS_NY=%d" % ny]))
+    return units
+
+
+def build(force: bool = False, verbose: bool = False, jobs: int | None = None) -> str:
     """Compile the CUDA library for sm_103a; returns its path."""
     if not force and up_to_date():
         return LIB
     os.makedirs(BUILD_DIR, exist_ok=True)
-    tmp = LIB + ".tmp%d" % os.getpid()
-    cmd = [nvcc(), *NVCC_FLAGS, "-I", os.path.join(ROOT, "include"), "-o", tmp, SRC]
+    cc = nvcc()
+    extra = ["-Xptxas=-v"] if verbose else []
+
+    def compile_one(u):
+        src, obj, flags = u
+        cmd = [cc, *CFLAGS, *extra, *flags, "-c", "-o", obj, src]
+        r = subprocess.run(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)
+        if r.returncode != 0:
+            raise RuntimeError("nvcc failed for %s:\n%s" % (os.path.basename(obj), r.stdout))
+        return obj, r.stdout
+
+    units = _units()
+    jobs = jobs or min(len(units), os.cpu_count() or 4)
+    with cf.ThreadPoolExecutor(max_workers=jobs) as ex:
+        results = list(ex.map(compile_one, units))
     if verbose:
-        cmd.insert(1, "-Xptxas=-v")
-    subprocess.check_call(cmd)
+        for obj, out in results:
+            print("==", os.path.basename(obj))
+            print(out)
+    tmp = LIB + ".tmp%d" % os.getpid()
+    subprocess.check_call([cc, *ARCH, "-shared", "-o", tmp] + [o for o, _ in results])
     os.replace(tmp, LIB)
     return LIB
 

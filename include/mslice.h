@@ -89,7 +89,7 @@ typedef struct mslice_params {
 size_t mslice_workspace_size(const mslice_params *p, int op);
 
 /* Forward model (Eq. 1 slice loop, then the far field of Fig. 1a).
- *   vol        [ns][nz][ny] complex: delta + i beta of each voxel (read only)
+ *   vol        [ns][nz][ny] complex: delta + i beta of each voxel (read only, 16-byte aligned)
  *   probe      NULL for the tilted unit plane wave exp(-i k sin(alpha_w) z_l),
  *              or [nw][nz][ny] complex user probe phi_0 (Sec. 5: any probe shape)
  *   intensity  [nw][nz][ny] float: I = |Psi|^2 (may be NULL)

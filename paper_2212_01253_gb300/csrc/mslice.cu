@@ -80,18 +80,33 @@ __global__ void k_setup(const SetupArgs S) {
     }
 }
 
-// t = exp(-i k Delta (delta - i beta)) = exp(-k Delta beta) (cos(k Delta delta) - i sin(...))
-__global__ void k_transmission(const float2* __restrict__ vol, float2* __restrict__ tv, size_t n, double kd) {
+// t = exp(-i k Delta (delta - i beta)) = exp(-k Delta beta) (cos(k Delta delta) - i sin(...)).
+// The phase arguments k Delta delta and k Delta beta are products with the
+// FP64 constant k Delta = kd_hi + kd_lo (two floats): fmaf(v, kd_hi, v * kd_lo)
+// is within one float ulp of the FP64 product, without FP64 arithmetic per
+// voxel.  Two voxels per thread and iteration (16-byte accesses).
+__global__ void k_transmission(const float4* __restrict__ vol, float4* __restrict__ tv, size_t n2, float kd_hi,
+                               float kd_lo) {
     const size_t stride = (size_t)gridDim.x * blockDim.x;
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const float2 v = __ldcs(vol + i);
-        const float ph = (float)(kd * (double)v.x);
-        const float mu = (float)(kd * (double)v.y);
-        float s, c;
-        sincosf(ph, &s, &c);
-        const float a = expf(-mu);
-        __stcg(tv + i, make_float2(a * c, -a * s));
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += stride) {
+        const float4 v = __ldcs(vol + i);
+        float s0, c0, s1, c1;
+        sincosf(fmaf(v.x, kd_hi, v.x * kd_lo), &s0, &c0);
+        sincosf(fmaf(v.z, kd_hi, v.z * kd_lo), &s1, &c1);
+        const float a0 = expf(-fmaf(v.y, kd_hi, v.y * kd_lo));
+        const float a1 = expf(-fmaf(v.w, kd_hi, v.w * kd_lo));
+        __stcg(tv + i, make_float4(a0 * c0, -a0 * s0, a1 * c1, -a1 * s1));
     }
+}
+
+// odd voxel count: the last voxel
+__global__ void k_transmission_tail(const float2* __restrict__ vol, float2* __restrict__ tv, float kd_hi,
+                                    float kd_lo) {
+    const float2 v = vol[0];
+    float s, c;
+    sincosf(fmaf(v.x, kd_hi, v.x * kd_lo), &s, &c);
+    const float a = expf(-fmaf(v.y, kd_hi, v.y * kd_lo));
+    tv[0] = make_float2(a * c, -a * s);
 }
 
 // g_psi = 2 dL/dI Psi: vector-Jacobian product of I = |Psi|^2
@@ -311,6 +326,23 @@ int launch_coop(const void* fn, int grid, size_t smem, const SweepArgs& a, cudaS
     return note(e, "cudaLaunchCooperativeKernel") ? MSLICE_ELAUNCH : MSLICE_OK;
 }
 
+int launch_transmission(const float2* vol, float2* tv, size_t nvox, double kd, cudaStream_t st) {
+    const float kd_hi = (float)kd;
+    const float kd_lo = (float)(kd - (double)kd_hi);
+    const size_t n2 = nvox / 2;
+    if (n2) {
+        size_t tb = (n2 + 255) / 256;
+        if (tb > 152 * 16) tb = 152 * 16;
+        k_transmission<<<(unsigned)tb, 256, 0, st>>>((const float4*)vol, (float4*)tv, n2, kd_hi, kd_lo);
+        if (note(cudaGetLastError(), "k_transmission launch")) return MSLICE_ELAUNCH;
+    }
+    if (nvox & 1) {
+        k_transmission_tail<<<1, 1, 0, st>>>(vol + nvox - 1, tv + nvox - 1, kd_hi, kd_lo);
+        if (note(cudaGetLastError(), "k_transmission_tail launch")) return MSLICE_ELAUNCH;
+    }
+    return MSLICE_OK;
+}
+
 struct Plan {
     KernelSet ks;
     Layout L;
@@ -325,7 +357,7 @@ int prepare(const mslice_params* p, int op, const float* vol, const float* probe
             float2* probe_z_out = nullptr) {
     int rc = validate(p);
     if (rc) return rc;
-    if (!vol || !ws || ((uintptr_t)ws & 255) || ((uintptr_t)vol & 7) || ((uintptr_t)probe & 7)) return MSLICE_EINVAL;
+    if (!vol || !ws || ((uintptr_t)ws & 255) || ((uintptr_t)vol & 15) || ((uintptr_t)probe & 7)) return MSLICE_EINVAL;
     P->L = make_layout(p, op);
     if (ws_bytes < P->L.total) return MSLICE_EWORKSPACE;
     P->ws = (char*)ws;
@@ -354,12 +386,10 @@ int prepare(const mslice_params* p, int op, const float* vol, const float* probe
     // transmission volume
     const double kd = 2.0 * M_PI / p->wavelength_nm * p->slice_nm;
     const size_t nvox = (size_t)p->ns * p->ny * p->nz;
-    int tb = (int)((nvox + 255) / 256);
-    if (tb > 4 * 152 * 8) tb = 4 * 152 * 8;
     r = prof_begin(KID_TRANSMISSION, (double)nvox, st);
-    k_transmission<<<tb, 256, 0, st>>>((const float2*)vol, (float2*)(w + L.tvol), nvox, kd);
+    rc = launch_transmission((const float2*)vol, (float2*)(w + L.tvol), nvox, kd, st);
     prof_end(r, st);
-    if (note(cudaGetLastError(), "k_transmission launch")) return MSLICE_ELAUNCH;
+    if (rc) return rc;
     SweepArgs& a = P->base;
     memset(&a, 0, sizeof(a));
     a.ny = p->ny; a.nz = p->nz; a.ns = p->ns; a.nw = p->nw;
@@ -522,13 +552,10 @@ int mslice_plan_tables(const mslice_params* p, float* py, float* pz, float* prob
 int mslice_transmission(const mslice_params* p, const float* vol, float* t_out, void* stream) {
     int rc = validate(p);
     if (rc) return rc;
-    if (!vol || !t_out) return MSLICE_EINVAL;
+    if (!vol || !t_out || ((uintptr_t)vol & 15) || ((uintptr_t)t_out & 15)) return MSLICE_EINVAL;
     const double kd = 2.0 * M_PI / p->wavelength_nm * p->slice_nm;
     const size_t nvox = (size_t)p->ns * p->ny * p->nz;
-    int tb = (int)((nvox + 255) / 256);
-    if (tb > 4 * 152 * 8) tb = 4 * 152 * 8;
-    k_transmission<<<tb, 256, 0, (cudaStream_t)stream>>>((const float2*)vol, (float2*)t_out, nvox, kd);
-    return cudaGetLastError() == cudaSuccess ? MSLICE_OK : MSLICE_ELAUNCH;
+    return launch_transmission((const float2*)vol, (float2*)t_out, nvox, kd, (cudaStream_t)stream);
 }
 
 int mslice_intensity_vjp(const float* psi, const float* dI, float* g_psi, size_t n, void* stream) {

@@ -32,7 +32,9 @@
 
 #include "mslice.h"
 
+#ifndef MS_THREADS
 #define MS_THREADS 256
+#endif
 #define MS_WARPS (MS_THREADS / 32)
 
 namespace {
@@ -257,6 +259,19 @@ __device__ __forceinline__ void named_bar(int id, int nthreads) {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
 
+// exchange synchronisation of one transform's threads: a warp (or part of
+// one), or a named barrier over the warps of a column group
+struct WarpSync {
+    __device__ __forceinline__ void operator()() const { __syncwarp(); }
+};
+struct GroupSync {
+    int id, nthreads;
+    __device__ __forceinline__ void operator()() const {
+        if (nthreads <= 32) __syncwarp();
+        else named_bar(id, nthreads);
+    }
+};
+
 // ctrl[0] = status bits, ctrl[1] = arrivals, ctrl[2] = exits
 struct Grid {
     unsigned* ctrl;
@@ -268,7 +283,7 @@ struct Grid {
     // Every block arrives, then waits until all nblocks (+ withhold) arrived or
     // the wait exceeded timeout_ns; returns false (uniformly per block) on
     // timeout or if another block already reported one.
-    __device__ bool sync(unsigned withhold = 0) {
+    __device__ __forceinline__ bool sync(unsigned withhold = 0) {
         __syncthreads();
         ++epoch;
         if (threadIdx.x == 0) {
@@ -296,7 +311,7 @@ struct Grid {
         return *(volatile int*)s_ok != 0;
     }
     // last block out resets the counters for the next launch on the stream
-    __device__ void finish() {
+    __device__ __forceinline__ void finish() {
         __syncthreads();
         if (threadIdx.x == 0) {
             __threadfence();
@@ -387,7 +402,7 @@ __device__ void row_pass(const SweepArgs& A, const Smem& S, const int j, const b
     const size_t npx = (size_t)A.ny * A.nz;
     const int ntasks = A.nz * A.nw;
     const int wtasks = (ntasks + tpw - 1) / tpw;
-    auto sync = []() { __syncwarp(); };
+    const WarpSync sync;
     for (int wt = blockIdx.x * MS_WARPS + warp; wt < wtasks; wt += gridDim.x * MS_WARPS) {
         const int task = wt * tpw + tm;
         const bool active = task < ntasks;
@@ -481,11 +496,13 @@ __device__ void row_pass(const SweepArgs& A, const Smem& S, const int j, const b
     }
 }
 
-// columns per column group: 16 (128-byte rows) while the group fits the CTA
-__host__ __device__ __forceinline__ int col_cw(int T) { return T <= 16 ? 16 : 8; }
-// exchange-region stride of one column: odd for 16-column groups, 2 mod 16
-// for 8-column groups, so the lanes of a half-warp hit distinct banks
-__host__ __device__ __forceinline__ int col_rs(int N, int cw) { return N + N / 32 + (cw == 16 ? 1 : 2); }
+// columns per column group: at least 4 (a full 32-byte sector per row and
+// thread row) and enough that the group fills a warp (cw * T >= 32), so that
+// the group's exchange barrier spans as few warps as possible
+__host__ __device__ __forceinline__ int col_cw(int T) { return 32 / T > 4 ? 32 / T : 4; }
+// exchange-region stride of one column, = 16/cw (mod 16) in 8-byte words, so
+// that the cw columns x 16/cw thread rows of a half-warp hit 16 distinct banks
+__host__ __device__ __forceinline__ int col_rs(int N, int cw) { return N + N / 32 + 16 / cw; }
 
 // ----- column pass: a group of cw*T threads per cw adjacent columns
 template <int OP, int NC = 0>
@@ -500,10 +517,7 @@ __device__ void col_pass(const SweepArgs& A, const Smem& S, double* s_red) {
     const size_t npx = (size_t)A.ny * A.nz;
     const int ncg = (A.ny + cw - 1) / cw;
     const int ntasks = ncg * A.nw;
-    auto sync = [gthreads, g]() {
-        if (gthreads <= 32) __syncwarp();
-        else named_bar(1 + g, gthreads);
-    };
+    const GroupSync sync{1 + g, gthreads};
     const float2* src = (OP == C_ADJ) ? A.gfield : (OP == C_SEED ? A.gpsi : A.field);
     double loss = 0.0;
     for (int task = blockIdx.x * groups + g; task < ntasks; task += gridDim.x * groups) {

@@ -142,13 +142,24 @@ def measured_peaks():
         return {}
 
 
+SWEEP_SOURCES = ("mslice_device.cuh", "mslice_inst.cu", "mslice_kernels.h", "mslice.cu")
+
+
+def source_hash():
+    """Hash of the sources of the slice-loop kernels (the ncu traffic record is
+    void once they change)."""
+    h = hashlib.sha256()
+    for f in SWEEP_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_2212_01253_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
 def traffic_record(kernel):
     """DRAM bytes per unit from a committed ncu summary, if the kernel source is unchanged."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
-    src = os.path.join(ROOT, "paper_2212_01253_gb300", "csrc", "mslice.cu")
     try:
         rec = json.load(open(path))
-        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        h = source_hash()
         if rec.get("source_sha256_16") != h:
             return None
         return rec["kernels"].get(kernel, {}).get("dram_bytes_per_unit")
@@ -159,20 +170,21 @@ def traffic_record(kernel):
 # ---------------------------------------------------------------------------
 # CPU oracle leg
 # ---------------------------------------------------------------------------
-def oracle_rate(ns_sample, reps=1):
-    """Oracle loss+gradient on 512^2 x ns_sample slices x 1 angle; units/s."""
+def oracle_rate(ns_sample, nangles=1, reps=1):
+    """Oracle loss+gradient on 512^2 x ns_sample slices x nangles angles; units per run."""
     import cssi_inputs as ci
     import oracle
 
-    geo = oracle.Geometry(NY, NZ, ns_sample, LAM, SLICE, DY, DZ, alpha_i_deg=(0.3,))
+    geo = oracle.Geometry(NY, NZ, ns_sample, LAM, SLICE, DY, DZ,
+                          alpha_i_deg=np.linspace(0.1, 0.5, nangles) if nangles > 1 else (0.3,))
     vol = ci.pillars_large(0, ns=ns_sample)
-    meas = np.ones((1, NZ, NY), np.float64)
+    meas = np.ones((nangles, NZ, NY), np.float64)
     times = []
     for _ in range(reps):
         t0 = time.perf_counter()
         oracle.loss_grad(geo, vol, meas, 1.0)
         times.append(time.perf_counter() - t0)
-    units = NY * NZ * ns_sample
+    units = NY * NZ * ns_sample * nangles
     return units, times, oracle.num_threads()
 
 
@@ -180,7 +192,7 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    ns_sample = 16
+    ns_sample = 256
     units, times, cores = oracle_rate(ns_sample, reps=args.warmup + args.steps)
     timed = times[args.warmup:]
     per_step = sum(timed) / len(timed)
@@ -337,12 +349,12 @@ def run_gpu(args):
     gpu_launches = sum(v[0] for v in prof.values())
 
     cpu = None
-    if not args.no_cpu_baseline and world == 1 or (not args.no_cpu_baseline and rank == 0):
-        ns_sample = args.cpu_slices
-        u, times, cores = oracle_rate(ns_sample, reps=1)
+    if not args.no_cpu_baseline:
+        ns_sample, na = args.cpu_slices, args.cpu_angles
+        u, times, cores = oracle_rate(ns_sample, nangles=na, reps=1)
         cpu = {"value": u / times[0], "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": "512x512 grid, %d of 1024 slices, 1 of 9 angles (FP64 oracle loss+gradient, "
-                         "%.1f s)" % (ns_sample, times[0])}
+               "sample": "512x512 grid, %d of 1024 slices, %d of 9 angles (FP64 oracle loss+gradient, "
+                         "%.1f s)" % (ns_sample, na, times[0])}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
@@ -363,7 +375,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--angles", type=int, default=NW)
     ap.add_argument("--slices", type=int, default=NS)
-    ap.add_argument("--cpu-slices", type=int, default=96)
+    ap.add_argument("--cpu-slices", type=int, default=1024)
+    ap.add_argument("--cpu-angles", type=int, default=3)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

@@ -69,6 +69,10 @@ extern "C" {
 #define MSLICE_EXIT_WAVE 1u  /* forward: field_out = phi_Ns (after the full last
                                 propagation) and intensity = |phi_Ns|^2 instead of
                                 the far field; used for near-field checks */
+#define MSLICE_PER_STRUCTURE 2u  /* wavefield w propagates through its own volume:
+                                    vol and grad_vol are [nw][ns][nz][ny] (nw
+                                    independent structures of one grid shape,
+                                    each with its own incidence angle) */
 
 typedef struct mslice_params {
     double wavelength_nm;      /* lambda; k = 2 pi / lambda is formed in FP64 */
@@ -81,7 +85,11 @@ typedef struct mslice_params {
     double alpha_i_rad[MSLICE_MAX_ANGLES]; /* incidence angle of each wavefield */
     double psi_rad;            /* in-plane (yaw) angle: must be 0 */
     int32_t checkpoint_every;  /* adjoint segment length in slices; <= 0 means 32 */
-    uint32_t flags;            /* MSLICE_EXIT_WAVE */
+    uint32_t flags;            /* MSLICE_EXIT_WAVE, MSLICE_PER_STRUCTURE */
+    int32_t grid_blocks;       /* launch shape: blocks of the persistent kernels, 0 = automatic
+                                  (capped at the co-resident maximum) */
+    int32_t col_width;         /* launch shape: columns per column-pass group (4, 8 or 16),
+                                  0 = automatic; see mslice_autotune in the Python package */
 } mslice_params;
 
 /* Bytes of workspace needed by `op` (MSLICE_OP_*) for these parameters;
@@ -118,6 +126,18 @@ int mslice_loss_grad(const mslice_params *p, const float *vol, const float *prob
                      const float *meas_amp, float scale, double *loss_out, float *grad_vol,
                      float *intensity, void *ws, size_t ws_bytes, void *stream);
 
+/* Loss and gradient of nw independent structures of one grid shape, advanced
+ * together (flag MSLICE_PER_STRUCTURE is implied):
+ *   vols       [nw][ns][nz][ny] complex, one volume per structure
+ *   meas_amp   [nw][nz][ny] float, scales: host float[nw] (s of each structure)
+ *   loss_out   device double[1]: sum over the structures
+ *   grad_vol   [nw][ns][nz][ny] complex out, one gradient per structure
+ * Workspace: mslice_workspace_size(p with the flag set, MSLICE_OP_LOSS_GRAD). */
+int mslice_loss_grad_multi(const mslice_params *p, const float *vols, const float *probe,
+                           const float *meas_amp, const float *scales, double *loss_out,
+                           float *grad_vol, float *intensity, void *ws, size_t ws_bytes,
+                           void *stream);
+
 /* The FP64-built constant arrays ("C" of Fig. 1), rounded to float:
  *   py [ny] complex: exp(-i Delta k_y^2 / 2k);  pz [nz] complex: exp(-i Delta k_z^2 / 2k)
  *   probe_z [nw][nz] complex: exp(-i k sin(alpha_w) z_l) (default probe, one value per row)
@@ -146,6 +166,42 @@ int mslice_status(const void *ws, void *stream);
  * limit and the status word records MSLICE_ETIMEDOUT.  ws >= 4096 bytes. */
 int mslice_debug_wait(int nblocks, int withhold, long long timeout_ns, void *ws,
                       size_t ws_bytes, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Reconstruction helpers (Sec. 4: coarse reconstruction voxels mapped onto the
+ * finer multislice grid, optimised with ADAM).
+ * ------------------------------------------------------------------------ */
+
+/* Coarse parameter grid: theta[cx][cz][cy] (real delta of each coarse voxel)
+ * maps onto the block of the fine volume starting at slice x0, row z0,
+ * column y0, each coarse voxel covering bx slices x bz rows x by columns.
+ * The fine voxel gets delta = theta and beta = beta_ratio * theta (one
+ * material with a fixed beta/delta ratio); voxels outside the block are not
+ * touched.  Sec. 4.1 and 4.2 use coarse voxels elongated along the beam. */
+typedef struct mslice_coarse {
+    int32_t cx, cz, cy;      /* coarse grid */
+    int32_t bx, bz, by;      /* block size in fine voxels */
+    int32_t x0, z0, y0;      /* fine-grid offset of the block */
+    float beta_ratio;        /* beta / delta of the material */
+} mslice_coarse;
+
+/* vol[x0 + bx*a + i][z0 + bz*b + k][y0 + by*c + l] = theta[a][b][c] * (1 + i beta_ratio).
+ * theta float [cx][cz][cy]; vol complex [ns][nz][ny] (p gives ns, nz, ny). */
+int mslice_coarse_to_fine(const mslice_params *p, const mslice_coarse *c, const float *theta,
+                          float *vol, void *stream);
+
+/* Adjoint of mslice_coarse_to_fine on a gradient grad_vol = dL/ddelta + i dL/dbeta:
+ * g_theta[a][b][c] = sum over the block of (dL/ddelta + beta_ratio dL/dbeta).
+ * Each coarse voxel is summed by one thread in a fixed order (deterministic). */
+int mslice_fine_to_coarse(const mslice_params *p, const mslice_coarse *c, const float *grad_vol,
+                          float *g_theta, void *stream);
+
+/* One ADAM step (Kingma & Ba, cited in Sec. 4.1) on n parameters, in place:
+ *   m = b1 m + (1-b1) g;  v = b2 v + (1-b2) g^2;
+ *   theta -= lr * (m / (1-b1^t)) / (sqrt(v / (1-b2^t)) + eps);  theta = clamp(theta, lo, hi)
+ * t >= 1 is the step number; m and v start at 0. */
+int mslice_adam_step(float *theta, float *m, float *v, const float *grad, size_t n, float lr,
+                     float b1, float b2, float eps, int t, float lo, float hi, void *stream);
 
 /* Per-kernel timing (tracing).  While enabled, every kernel launch of the
  * library is bracketed by a CUDA event pair recorded on the launching stream;

@@ -202,3 +202,51 @@ def dft2d(x, sign=-1, naive=False):
     nz, ny = x.shape
     _rc(_load().orc_dft2d(ny, nz, _ptr(x), int(sign), int(bool(naive))), "orc_dft2d")
     return x
+
+
+# ---------------------------------------------------------------------------
+# Reconstruction helpers (Sec. 4): coarse reconstruction voxels on the fine
+# multislice grid, and the ADAM update the paper optimises them with.
+# Plain numpy in double precision; definitions written out.
+# ---------------------------------------------------------------------------
+def coarse_to_fine(theta, fine_shape, block, offset=(0, 0, 0), beta_ratio=4.9e-6 / 4.7e-5, base=None):
+    """E: theta[cx][cz][cy] -> volume [ns][nz][ny]; every fine voxel of a coarse
+    block gets delta = theta and beta = beta_ratio * theta; others keep ``base``."""
+    theta = np.asarray(theta, dtype=np.float64)
+    vol = np.zeros(fine_shape, np.complex128) if base is None else np.array(base, np.complex128)
+    cx, cz, cy = theta.shape
+    bx, bz, by = block
+    x0, z0, y0 = offset
+    for a in range(cx):
+        for b in range(cz):
+            for c in range(cy):
+                d = theta[a, b, c]
+                vol[x0 + a * bx:x0 + (a + 1) * bx, z0 + b * bz:z0 + (b + 1) * bz,
+                    y0 + c * by:y0 + (c + 1) * by] = d + 1j * beta_ratio * d
+    return vol
+
+
+def fine_to_coarse(grad, coarse_shape, block, offset=(0, 0, 0), beta_ratio=4.9e-6 / 4.7e-5):
+    """E^T: sum of dL/ddelta + beta_ratio dL/dbeta over each coarse block."""
+    grad = np.asarray(grad, dtype=np.complex128)
+    cx, cz, cy = coarse_shape
+    bx, bz, by = block
+    x0, z0, y0 = offset
+    g = np.zeros(coarse_shape, np.float64)
+    for a in range(cx):
+        for b in range(cz):
+            for c in range(cy):
+                blk = grad[x0 + a * bx:x0 + (a + 1) * bx, z0 + b * bz:z0 + (b + 1) * bz,
+                           y0 + c * by:y0 + (c + 1) * by]
+                g[a, b, c] = (blk.real + beta_ratio * blk.imag).sum()
+    return g
+
+
+def adam_step(theta, m, v, grad, lr, b1, b2, eps, t, lo=-np.inf, hi=np.inf):
+    """One ADAM step (Kingma & Ba): returns new (theta, m, v)."""
+    m = b1 * m + (1 - b1) * grad
+    v = b2 * v + (1 - b2) * grad * grad
+    mhat = m / (1 - b1 ** t)
+    vhat = v / (1 - b2 ** t)
+    theta = np.clip(theta - lr * mhat / (np.sqrt(vhat) + eps), lo, hi)
+    return theta, m, v

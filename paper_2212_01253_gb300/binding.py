@@ -20,6 +20,7 @@ from . import build as _build
 MSLICE_MAX_ANGLES = 64
 MSLICE_OP_FORWARD, MSLICE_OP_ADJOINT, MSLICE_OP_LOSS_GRAD = 0, 1, 2
 MSLICE_EXIT_WAVE = 1
+MSLICE_PER_STRUCTURE = 2
 ERRORS = {-1: "MSLICE_EINVAL", -2: "MSLICE_EUNSUPPORTED", -3: "MSLICE_ELAUNCH",
           -4: "MSLICE_ETIMEDOUT", -5: "MSLICE_EWORKSPACE"}
 
@@ -47,11 +48,14 @@ class mslice_params(ctypes.Structure):
         ("psi_rad", ctypes.c_double),
         ("checkpoint_every", ctypes.c_int32),
         ("flags", ctypes.c_uint32),
+        ("grid_blocks", ctypes.c_int32),
+        ("col_width", ctypes.c_int32),
     ]
 
 
 def make_params(ny, nz, ns, alpha_i_deg=(0.3,), wavelength_nm=0.155, slice_nm=20.0,
-                dy_nm=2.0, dz_nm=2.0, checkpoint_every=32, flags=0, psi_rad=0.0):
+                dy_nm=2.0, dz_nm=2.0, checkpoint_every=32, flags=0, psi_rad=0.0, grid_blocks=0,
+                col_width=0):
     """mslice_params from plain numbers (angles in degrees)."""
     alphas = [math.radians(float(a)) for a in (alpha_i_deg if hasattr(alpha_i_deg, "__len__")
                                                else [alpha_i_deg])]
@@ -65,7 +69,26 @@ def make_params(ny, nz, ns, alpha_i_deg=(0.3,), wavelength_nm=0.155, slice_nm=20
     p.psi_rad = psi_rad
     p.checkpoint_every = int(checkpoint_every)
     p.flags = int(flags)
+    p.grid_blocks = int(grid_blocks)
+    p.col_width = int(col_width)
     return p
+
+
+class mslice_coarse(ctypes.Structure):
+    _fields_ = [("cx", ctypes.c_int32), ("cz", ctypes.c_int32), ("cy", ctypes.c_int32),
+                ("bx", ctypes.c_int32), ("bz", ctypes.c_int32), ("by", ctypes.c_int32),
+                ("x0", ctypes.c_int32), ("z0", ctypes.c_int32), ("y0", ctypes.c_int32),
+                ("beta_ratio", ctypes.c_float)]
+
+
+def make_coarse(shape, block, offset=(0, 0, 0), beta_ratio=4.9e-6 / 4.7e-5):
+    """mslice_coarse for a coarse grid shape (cx, cz, cy), block (bx, bz, by) and fine offset."""
+    c = mslice_coarse()
+    c.cx, c.cz, c.cy = (int(v) for v in shape)
+    c.bx, c.bz, c.by = (int(v) for v in block)
+    c.x0, c.z0, c.y0 = (int(v) for v in offset)
+    c.beta_ratio = float(beta_ratio)
+    return c
 
 
 class mslice_kernel_time(ctypes.Structure):
@@ -93,6 +116,7 @@ def _load():
                 "mslice_loss_grad": ([P, vp, vp, vp, ctypes.c_float, vp, vp, vp, vp, sz, vp],
                                      ctypes.c_int),
                 "mslice_plan_tables": ([P, vp, vp, vp, vp, sz, vp], ctypes.c_int),
+                "mslice_loss_grad_multi": ([P, vp, vp, vp, vp, vp, vp, vp, vp, sz, vp], ctypes.c_int),
                 "mslice_transmission": ([P, vp, vp, vp], ctypes.c_int),
                 "mslice_status": ([vp, vp], ctypes.c_int),
                 "mslice_intensity_vjp": ([vp, vp, vp, sz, vp], ctypes.c_int),
@@ -101,6 +125,11 @@ def _load():
                 "mslice_strerror": ([ctypes.c_int], ctypes.c_char_p),
                 "mslice_last_cuda_error": ([], ctypes.c_char_p),
                 "mslice_profile_enable": ([ctypes.c_int], ctypes.c_int),
+                "mslice_coarse_to_fine": ([P, ctypes.POINTER(mslice_coarse), vp, vp, vp], ctypes.c_int),
+                "mslice_fine_to_coarse": ([P, ctypes.POINTER(mslice_coarse), vp, vp, vp], ctypes.c_int),
+                "mslice_adam_step": ([vp, vp, vp, vp, sz, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                      ctypes.c_float, ctypes.c_int, ctypes.c_float, ctypes.c_float, vp],
+                                     ctypes.c_int),
                 "mslice_profile_read": ([ctypes.POINTER(mslice_kernel_time), ctypes.c_int],
                                         ctypes.c_int),
             }
@@ -159,7 +188,8 @@ def workspace(p: mslice_params, op: int, device=None) -> torch.Tensor:
 
 def _sizes(p):
     npx = p.ny * p.nz
-    return p.ns * npx, p.nw * npx
+    nvol = p.ns * npx * (p.nw if p.flags & MSLICE_PER_STRUCTURE else 1)
+    return nvol, p.nw * npx
 
 
 def mslice_forward(p, vol, probe, intensity, field_out, ws, stream=None):
@@ -192,6 +222,23 @@ def mslice_loss_grad(p, vol, probe, meas_amp, scale, loss_out, grad_vol, intensi
         _ptr(grad_vol, torch.complex64, nvol, "grad_vol"),
         _ptr(intensity, torch.float32, nfield, "intensity"),
         _ptr(ws, torch.uint8, None, "ws"), ws.numel(), _stream(stream)), "mslice_loss_grad")
+
+
+def mslice_loss_grad_multi(p, vols, probe, meas_amp, scales, loss_out, grad_vol, intensity, ws, stream=None):
+    """Loss (summed) and per-structure gradients of nw structures; p.flags must
+    carry MSLICE_PER_STRUCTURE so that the array sizes are per structure."""
+    if not p.flags & MSLICE_PER_STRUCTURE:
+        raise ValueError("set MSLICE_PER_STRUCTURE in p.flags")
+    nvol, nfield = _sizes(p)
+    sc = (ctypes.c_float * p.nw)(*[float(x) for x in scales])
+    _check(_load().mslice_loss_grad_multi(
+        ctypes.byref(p), _ptr(vols, torch.complex64, nvol, "vols"),
+        _ptr(probe, torch.complex64, nfield, "probe"),
+        _ptr(meas_amp, torch.float32, nfield, "meas_amp"), ctypes.cast(sc, ctypes.c_void_p),
+        _ptr(loss_out, torch.float64, 1, "loss_out"),
+        _ptr(grad_vol, torch.complex64, nvol, "grad_vol"),
+        _ptr(intensity, torch.float32, nfield, "intensity"),
+        _ptr(ws, torch.uint8, None, "ws"), ws.numel(), _stream(stream)), "mslice_loss_grad_multi")
 
 
 def mslice_plan_tables(p, py, pz, probe_z, ws, stream=None):
@@ -240,3 +287,26 @@ def mslice_profile_read():
         raise MsliceError(n, "mslice_profile_read")
     return {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].total_ms), float(buf[i].units))
             for i in range(n)}
+
+
+def mslice_coarse_to_fine(p, c, theta, vol, stream=None):
+    nvol, _ = _sizes(p)
+    _check(_load().mslice_coarse_to_fine(
+        ctypes.byref(p), ctypes.byref(c), _ptr(theta, torch.float32, c.cx * c.cz * c.cy, "theta"),
+        _ptr(vol, torch.complex64, nvol, "vol"), _stream(stream)), "mslice_coarse_to_fine")
+
+
+def mslice_fine_to_coarse(p, c, grad_vol, g_theta, stream=None):
+    nvol, _ = _sizes(p)
+    _check(_load().mslice_fine_to_coarse(
+        ctypes.byref(p), ctypes.byref(c), _ptr(grad_vol, torch.complex64, nvol, "grad_vol"),
+        _ptr(g_theta, torch.float32, c.cx * c.cz * c.cy, "g_theta"), _stream(stream)),
+        "mslice_fine_to_coarse")
+
+
+def mslice_adam_step(theta, m, v, grad, lr, b1, b2, eps, t, lo, hi, stream=None):
+    n = theta.numel()
+    _check(_load().mslice_adam_step(
+        _ptr(theta, torch.float32, n, "theta"), _ptr(m, torch.float32, n, "m"),
+        _ptr(v, torch.float32, n, "v"), _ptr(grad, torch.float32, n, "grad"), n, float(lr), float(b1),
+        float(b2), float(eps), int(t), float(lo), float(hi), _stream(stream)), "mslice_adam_step")

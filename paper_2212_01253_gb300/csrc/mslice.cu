@@ -138,7 +138,9 @@ int validate(const mslice_params* p) {
     for (int w = 0; w < p->nw; ++w)
         if (!(fabs(p->alpha_i_rad[w]) < 1.5707963)) return MSLICE_EINVAL;
     if (p->psi_rad != 0.0) return MSLICE_EUNSUPPORTED;
-    if (p->flags & ~MSLICE_EXIT_WAVE) return MSLICE_EINVAL;
+    if (p->flags & ~(MSLICE_EXIT_WAVE | MSLICE_PER_STRUCTURE)) return MSLICE_EINVAL;
+    if (p->grid_blocks < 0 || p->col_width < 0) return MSLICE_EINVAL;
+    if (p->col_width > 0 && !col_cw_ok(p->col_width, p->nz > 32 ? p->nz / 32 : 1)) return MSLICE_EINVAL;
     return MSLICE_OK;
 }
 
@@ -159,11 +161,12 @@ Layout make_layout(const mslice_params* p, int op) {
     L.partials = off; off = align256(off + kPartialBytes);
     L.tab = off; off = align256(off + 2 * (size_t)(p->ny + p->nz) * sizeof(float2));
     L.probe_z = off; off = align256(off + (size_t)p->nw * p->nz * sizeof(float2));
-    L.tvol = off; off = align256(off + (size_t)p->ns * npx * sizeof(float2));
+    const size_t nvol = (p->flags & MSLICE_PER_STRUCTURE) ? (size_t)p->nw : 1;
+    L.tvol = off; off = align256(off + nvol * p->ns * npx * sizeof(float2));
     L.field = off; off = align256(off + fb);
     if (op == MSLICE_OP_ADJOINT || op == MSLICE_OP_LOSS_GRAD) {
         L.gfield = off; off = align256(off + fb);
-        L.gpart = off; off = align256(off + (p->nw > 1 ? fb : 0));
+        L.gpart = off; off = align256(off + (p->nw > 1 && !(p->flags & MSLICE_PER_STRUCTURE) ? fb : 0));
         L.ckpt = off; off = align256(off + (size_t)L.nseg * fb);
         L.seg = off; off = align256(off + (size_t)L.K * fb);
     }
@@ -171,12 +174,12 @@ Layout make_layout(const mslice_params* p, int op) {
     return L;
 }
 
-size_t smem_bytes(int ny, int nz) {
+size_t smem_bytes(int ny, int nz, int cw) {
     const size_t tabs = 2 * (size_t)(ny + nz) * sizeof(float2);
     size_t row = 0, col = 0;
     if (ny > 32) row = (size_t)(MS_THREADS / (ny / 32)) * (ny + ny / 32) * sizeof(float2);
     if (nz > 32) {
-        const int T = nz / 32, cw = col_cw(T), groups = MS_THREADS / (cw * T);
+        const int T = nz / 32, groups = MS_THREADS / (cw * T);
         col = (size_t)groups * cw * col_rs(nz, cw) * sizeof(float2);
     }
     return tabs + (row > col ? row : col);
@@ -269,6 +272,13 @@ int device_info(size_t smem, const KernelSet& ks, DevInfo** out) {
     return MSLICE_OK;
 }
 
+// column-group width of a call: the requested one if usable, else the default
+int col_width(const mslice_params* p) {
+    const int Tz = p->nz > 32 ? p->nz / 32 : 1;
+    if (p->col_width > 0 && col_cw_ok(p->col_width, Tz)) return p->col_width;
+    return col_cw(Tz);
+}
+
 int grid_size(const mslice_params* p, const DevInfo& D) {
     int maxg = D.sms * D.occ;
     if (maxg > kMaxGrid) maxg = kMaxGrid;
@@ -276,13 +286,14 @@ int grid_size(const mslice_params* p, const DevInfo& D) {
     const int Ty = p->ny > 32 ? p->ny / 32 : 1, Tz = p->nz > 32 ? p->nz / 32 : 1;
     const long rows = (long)p->nz * p->nw;
     const long row_wtasks = (rows + (32 / Ty) - 1) / (32 / Ty);
-    const int cw = col_cw(Tz);
+    const int cw = col_width(p);
     const long col_tasks = (long)((p->ny + cw - 1) / cw) * p->nw;
     const long col_groups = MS_THREADS / (cw * Tz);
     long need = (row_wtasks + 3) / 4;
     const long need_c = (col_tasks + col_groups - 1) / col_groups;
     if (need_c > need) need = need_c;
     if (need < 1) need = 1;
+    if (p->grid_blocks > 0) need = p->grid_blocks;
     return (int)(need < maxg ? need : maxg);
 }
 
@@ -361,7 +372,8 @@ int prepare(const mslice_params* p, int op, const float* vol, const float* probe
     P->L = make_layout(p, op);
     if (ws_bytes < P->L.total) return MSLICE_EWORKSPACE;
     P->ws = (char*)ws;
-    P->smem = smem_bytes(p->ny, p->nz);
+    const int cw = col_width(p);
+    P->smem = smem_bytes(p->ny, p->nz, cw);
     DevInfo* D = nullptr;
     P->ks = sweep_kernels(p->ny, p->nz);
     if ((rc = device_info(P->smem, P->ks, &D))) return rc;
@@ -385,7 +397,7 @@ int prepare(const mslice_params* p, int op, const float* vol, const float* probe
     if (note(cudaGetLastError(), "k_setup launch")) return MSLICE_ELAUNCH;
     // transmission volume
     const double kd = 2.0 * M_PI / p->wavelength_nm * p->slice_nm;
-    const size_t nvox = (size_t)p->ns * p->ny * p->nz;
+    const size_t nvox = (size_t)p->ns * p->ny * p->nz * ((p->flags & MSLICE_PER_STRUCTURE) ? p->nw : 1);
     r = prof_begin(KID_TRANSMISSION, (double)nvox, st);
     rc = launch_transmission((const float2*)vol, (float2*)(w + L.tvol), nvox, kd, st);
     prof_end(r, st);
@@ -413,6 +425,8 @@ int prepare(const mslice_params* p, int op, const float* vol, const float* probe
     a.K = L.K;
     a.init_ckpt = -1;
     a.seg_from = 0x7fffffff;
+    a.per_w = (p->flags & MSLICE_PER_STRUCTURE) ? 1 : 0;
+    a.lcw = ilog2(cw);
     return MSLICE_OK;
 }
 
@@ -526,6 +540,29 @@ int mslice_loss_grad(const mslice_params* p, const float* vol, const float* prob
     P.base.grad = (float2*)grad_vol;
     P.base.intensity = intensity;
     return run_gradient(p, P, true, st);
+}
+
+int mslice_loss_grad_multi(const mslice_params* p, const float* vols, const float* probe, const float* meas_amp,
+                           const float* scales, double* loss_out, float* grad_vol, float* intensity, void* ws,
+                           size_t ws_bytes, void* stream) {
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!p || !meas_amp || !scales || !loss_out || !grad_vol) return MSLICE_EINVAL;
+    if (p->flags & MSLICE_EXIT_WAVE) return MSLICE_EUNSUPPORTED;
+    mslice_params q = *p;
+    q.flags |= MSLICE_PER_STRUCTURE;
+    if (q.nw < 1 || q.nw > MSLICE_MAX_ANGLES) return MSLICE_EINVAL;
+    for (int w = 0; w < q.nw; ++w)
+        if (!(scales[w] > 0.f)) return MSLICE_EINVAL;
+    Plan P;
+    int rc = prepare(&q, MSLICE_OP_LOSS_GRAD, vols, probe, ws, ws_bytes, st, &P);
+    if (rc) return rc;
+    P.base.meas = meas_amp;
+    P.base.scale = scales[0];
+    for (int w = 0; w < q.nw; ++w) P.base.scales[w] = scales[w];
+    P.base.loss_out = loss_out;
+    P.base.grad = (float2*)grad_vol;
+    P.base.intensity = intensity;
+    return run_gradient(&q, P, true, st);
 }
 
 int mslice_plan_tables(const mslice_params* p, float* py, float* pz, float* probe_z, void* ws, size_t ws_bytes,

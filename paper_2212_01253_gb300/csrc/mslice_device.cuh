@@ -60,18 +60,36 @@ __device__ __forceinline__ float2 cmulc(float2 a, float2 w) {
     return make_float2(fmaf(a.x, w.x, a.y * w.y), fmaf(a.y, w.x, -a.x * w.y));
 }
 
-// cos(pi e / 16), e = 0..16 (correctly rounded from the double values)
-__host__ __device__ constexpr float kcos32(int e) {
-    return e == 0 ? 1.0f
-         : e == 1 ? (float)0.9807852804032304
-         : e == 2 ? (float)0.9238795325112867
-         : e == 3 ? (float)0.8314696123025452
-         : e == 4 ? (float)0.7071067811865476
-         : e == 5 ? (float)0.5555702330196023
-         : e == 6 ? (float)0.38268343236508984
-         : e == 7 ? (float)0.19509032201612833
-         : e == 8 ? 0.0f
-         : -kcos32(16 - e);
+// cos(pi e / 16) for e = 0..16, correctly rounded from the double values.  A
+// flat switch (no recursion) that is inlined and folds to an immediate when e
+// is a compile-time constant after unrolling.
+__host__ __device__ __forceinline__ constexpr float kcos32(int e) {
+    switch (e) {
+        case 0: return 1.0f;
+        case 1: return (float)0.9807852804032304;
+        case 2: return (float)0.9238795325112867;
+        case 3: return (float)0.8314696123025452;
+        case 4: return (float)0.7071067811865476;
+        case 5: return (float)0.5555702330196023;
+        case 6: return (float)0.38268343236508984;
+        case 7: return (float)0.19509032201612833;
+        case 8: return 0.0f;
+        case 9: return -(float)0.19509032201612833;
+        case 10: return -(float)0.38268343236508984;
+        case 11: return -(float)0.5555702330196023;
+        case 12: return -(float)0.7071067811865476;
+        case 13: return -(float)0.8314696123025452;
+        case 14: return -(float)0.9238795325112867;
+        case 15: return -(float)0.9807852804032304;
+        default: return -1.0f;  // e = 16
+    }
+}
+
+// log2 of a power of two (loop, inlined)
+__host__ __device__ __forceinline__ constexpr int ilog2(int n) {
+    int l = 0;
+    while (n > 1) { n >>= 1; ++l; }
+    return l;
 }
 
 template <int R> struct Log2 { static constexpr int value = 1 + Log2<R / 2>::value; };
@@ -362,7 +380,16 @@ struct SweepArgs {
     int seg_base;           // slice of seg[0]
     int seg_from;           // forward: store a_j for j >= seg_from
     int prop_last;          // forward: the last slice of the range also propagates
+    int per_w;              // 1: wavefield w has its own volume (tvol, grad: [nw][ns][nz][ny])
+    int lcw;                // log2 of the columns per column-pass group
+    float scales[MSLICE_MAX_ANGLES];  // per-wavefield loss scale when per_w
 };
+
+// transmission row / gradient row of wavefield w at slice j, row z
+__device__ __forceinline__ size_t vol_offset(const SweepArgs& A, int w, int j, int z, int N) {
+    const size_t npx = (size_t)A.ny * A.nz;
+    return (A.per_w ? (size_t)w * A.ns * npx : 0) + (size_t)j * npx + (size_t)z * N;
+}
 
 struct Smem {
     float2* exch;    // exchange regions
@@ -433,7 +460,7 @@ __device__ void row_pass(const SweepArgs& A, const Smem& S, const int j, const b
 #pragma unroll
                     for (int m = 0; m < 32; ++m) if (m < P) __stcg(dst + t + T * m, x[m]);
                 }
-                const float2* tv = A.tvol + (size_t)j * npx + (size_t)z * N;
+                const float2* tv = A.tvol + vol_offset(A, w, j, z, N);
 #pragma unroll
                 for (int m = 0; m < 32; ++m) if (m < P) x[m] = cmul(x[m], __ldg(tv + t + T * m));
                 if (j >= A.seg_from) {
@@ -460,7 +487,7 @@ __device__ void row_pass(const SweepArgs& A, const Smem& S, const int j, const b
                 for (int m = 0; m < 32; ++m) if (m < P) x[m] = __ldcg(A.gfield + row + t + T * m);
                 // x = g_{a_j}; gradient contribution -i kd a_j conj(g)
                 const float2* a = A.seg + (size_t)(j - A.seg_base) * A.nw * npx + row;
-                float2* gdst = (A.nw == 1) ? (A.grad + (size_t)j * npx + (size_t)z * N) : (A.gpart + row);
+                float2* gdst = (A.nw == 1 || A.per_w) ? (A.grad + vol_offset(A, w, j, z, N)) : (A.gpart + row);
 #pragma unroll
                 for (int m = 0; m < 32; ++m) {
                     if (m < P) {
@@ -471,7 +498,7 @@ __device__ void row_pass(const SweepArgs& A, const Smem& S, const int j, const b
                     }
                 }
                 if (prop) {
-                    const float2* tv = A.tvol + (size_t)j * npx + (size_t)z * N;
+                    const float2* tv = A.tvol + vol_offset(A, w, j, z, N);
 #pragma unroll
                     for (int m = 0; m < 32; ++m) if (m < P) x[m] = cmulc(x[m], __ldg(tv + t + T * m));
                 }
@@ -496,10 +523,16 @@ __device__ void row_pass(const SweepArgs& A, const Smem& S, const int j, const b
     }
 }
 
-// columns per column group: at least 4 (a full 32-byte sector per row and
-// thread row) and enough that the group fills a warp (cw * T >= 32), so that
-// the group's exchange barrier spans as few warps as possible
+// default columns per column group: at least 4 (a full 32-byte sector per row
+// and thread row) and enough that the group fills a warp (cw * T >= 32), so
+// that the group's exchange barrier spans as few warps as possible
 __host__ __device__ __forceinline__ int col_cw(int T) { return 32 / T > 4 ? 32 / T : 4; }
+// a column-group width is usable if it is a power of two >= 4 (>= 32 / T for
+// small T) whose group divides the block
+__host__ __device__ __forceinline__ bool col_cw_ok(int cw, int T) {
+    return cw >= 1 && cw <= 32 && (cw & (cw - 1)) == 0 && cw * T <= MS_THREADS && MS_THREADS % (cw * T) == 0 &&
+           cw >= (32 / T > 4 ? 4 : 32 / T) && (T > 1 || cw == 32);
+}
 // exchange-region stride of one column, = 16/cw (mod 16) in 8-byte words, so
 // that the cw columns x 16/cw thread rows of a half-warp hit 16 distinct banks
 __host__ __device__ __forceinline__ int col_rs(int N, int cw) { return N + N / 32 + 16 / cw; }
@@ -508,11 +541,11 @@ __host__ __device__ __forceinline__ int col_rs(int N, int cw) { return N + N / 3
 template <int OP, int NC = 0>
 __device__ void col_pass(const SweepArgs& A, const Smem& S, double* s_red) {
     const int N = NC ? NC : A.nz, T = row_T(N), P = N > 32 ? 32 : N;
-    const int cw = col_cw(T);
-    const int gthreads = cw * T;
-    const int groups = MS_THREADS / gthreads;
-    const int g = threadIdx.x / gthreads, gt = threadIdx.x % gthreads;
-    const int c = gt % cw, t = gt / cw;
+    const int lcw = A.lcw, cw = 1 << lcw;
+    const int lg = lcw + ilog2(T), gthreads = 1 << lg;
+    const int groups = MS_THREADS >> lg;
+    const int g = threadIdx.x >> lg, gt = threadIdx.x & (gthreads - 1);
+    const int c = gt & (cw - 1), t = gt >> lcw;
     float2* reg = S.exch + (size_t)(g * cw + c) * col_rs(N, cw);
     const size_t npx = (size_t)A.ny * A.nz;
     const int ncg = (A.ny + cw - 1) / cw;
@@ -549,10 +582,11 @@ __device__ void col_pass(const SweepArgs& A, const Smem& S, double* s_red) {
                         if constexpr (OP == C_FAR_LOSS) {
                             float2 gs = make_float2(0.f, 0.f);
                             if (active) {
-                                const float r = sqrtf(A.scale * I);
+                                const float sc = A.per_w ? A.scales[w] : A.scale;
+                                const float r = sqrtf(sc * I);
                                 const float d = r - __ldg(A.meas + o);
                                 loss += (double)d * (double)d;
-                                if (r > 0.f) gs = cscale(psi, 2.f * A.scale * d / r);
+                                if (r > 0.f) gs = cscale(psi, 2.f * sc * d / r);
                             }
                             x[m] = gs;
                         }
@@ -642,7 +676,11 @@ __global__ void __launch_bounds__(MS_THREADS, 1) k_fwd_t(const SweepArgs A) {
         row_pass<R_FWD, NY>(A, S, j, j == A.j_begin, prop);
         if (prop) {
             if (!grid.sync()) return;
-            if (j + 1 < A.j_end) prefetch_l2(A.tvol + (size_t)(j + 1) * A.ny * A.nz, slice_bytes);
+            if (j + 1 < A.j_end) {
+                const size_t npx = (size_t)A.ny * A.nz;
+                for (int w = 0; w < (A.per_w ? A.nw : 1); ++w)
+                    prefetch_l2(A.tvol + (size_t)w * A.ns * npx * A.per_w + (size_t)(j + 1) * npx, slice_bytes);
+            }
             col_pass<C_PROP, NZ>(A, S, s_red);
             if (j < A.j_end - 1 && !grid.sync()) return;
         }
@@ -694,11 +732,12 @@ __global__ void __launch_bounds__(MS_THREADS, 1) k_adj_t(const SweepArgs A) {
         row_pass<R_ADJ, NY>(A, S, j, false, j > 0);
         if (!grid.sync()) return;
         if (j - 1 >= A.j_begin) {
-            prefetch_l2(A.tvol + (size_t)(j - 1) * npx, npx * sizeof(float2));
+            for (int w = 0; w < (A.per_w ? A.nw : 1); ++w)
+                prefetch_l2(A.tvol + (size_t)w * A.ns * npx * A.per_w + (size_t)(j - 1) * npx, npx * sizeof(float2));
             prefetch_l2(A.seg + (size_t)(j - 1 - A.seg_base) * A.nw * npx, A.nw * npx * sizeof(float2));
         }
         if (j > 0) col_pass<C_ADJ, NZ>(A, S, s_red);
-        if (A.nw > 1) reduce_gpart(A, j);
+        if (A.nw > 1 && !A.per_w) reduce_gpart(A, j);
         if (j > A.j_begin && !grid.sync()) return;
     }
     grid.finish();

@@ -320,3 +320,40 @@ def test_loss_seed_zero_amplitude(oracle_lib):
     L, g = oracle_lib.loss_grad(geo, np.zeros((ns, nz, ny)), np.ones((1, nz, ny)), 1.0, probe=probe)
     assert L == pytest.approx(nz * ny)
     assert np.all(g == 0)
+
+
+# --------------------------------------------------------------------------
+# Reconstruction helpers: coarse-to-fine map and ADAM
+# --------------------------------------------------------------------------
+def test_coarse_map_transpose_identity(oracle_lib):
+    """<E theta, g>_R = <theta, E^T g> with <u, g>_R = sum Re(u) Re(g) + Im(u) Im(g)."""
+    rng = np.random.default_rng(7)
+    shape, block, off = (3, 2, 4), (2, 3, 2), (1, 2, 0)
+    fine = (8, 9, 9)
+    theta = rng.normal(size=shape)
+    g = rng.normal(size=fine) + 1j * rng.normal(size=fine)
+    Et = oracle_lib.coarse_to_fine(theta, fine, block, off, beta_ratio=0.3)
+    lhs = float((Et.real * g.real + Et.imag * g.imag).sum())
+    rhs = float((theta * oracle_lib.fine_to_coarse(g, shape, block, off, beta_ratio=0.3)).sum())
+    assert abs(lhs - rhs) < 1e-12 * abs(lhs)
+    # a constant theta fills exactly its block
+    one = oracle_lib.coarse_to_fine(np.ones(shape), fine, block, off, beta_ratio=0.3)
+    assert np.count_nonzero(one) == np.prod(shape) * np.prod(block)
+    assert np.allclose(one[one != 0], 1 + 0.3j)
+
+
+def test_adam_first_step_and_convergence(oracle_lib):
+    """First step: m_hat = g, v_hat = g^2, so the step is lr * g / (|g| + eps);
+    on f = sum (theta - c)^2 ADAM reaches the minimum."""
+    g = np.array([2.0, -0.5, 1e-3])
+    th, m, v = oracle_lib.adam_step(np.zeros(3), np.zeros(3), np.zeros(3), g, 0.1, 0.9, 0.999, 1e-8, 1)
+    assert np.allclose(th, -0.1 * g / (np.abs(g) + 1e-8))
+    c = np.array([0.3, -1.2, 2.0])
+    th, m, v = np.zeros(3), np.zeros(3), np.zeros(3)
+    for t in range(1, 3001):
+        th, m, v = oracle_lib.adam_step(th, m, v, 2 * (th - c), 0.01, 0.9, 0.999, 1e-8, t)
+    assert np.abs(th - c).max() < 1e-3
+    # clamping to [lo, hi]
+    th, _, _ = oracle_lib.adam_step(np.zeros(1), np.zeros(1), np.zeros(1), np.array([-1.0]), 1.0, 0.9, 0.999,
+                                    1e-8, 1, lo=0.0, hi=0.5)
+    assert th[0] == 0.5

@@ -106,6 +106,25 @@ int mslice_forward(const mslice_params *p, const float *vol, const float *probe,
                    float *intensity, float *field_out, void *ws, size_t ws_bytes,
                    void *stream);
 
+/* mslice_forward without a caller workspace and without any allocation.  The
+ * paper has no counterpart: this entry point is for callers that cannot
+ * allocate device memory -- code running while a foreign framework captures a
+ * CUDA graph (where a cudaMalloc would break the capture), or real-time and
+ * plugin hosts whose device allocator is off limits to them.  The workspace is
+ * a fixed 32 MiB device array inside the library (every GPU that loads the
+ * library holds it until the process exits); parameters whose forward
+ * workspace (mslice_workspace_size(p, MSLICE_OP_FORWARD)) exceeds 32 MiB are
+ * rejected with MSLICE_EWORKSPACE (32 MiB covers e.g. 512x512 x 14 slices or
+ * 256x256 x 60 slices).  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress, with that device current); make that
+ * first call before any stream capture.  Every call shares the one array and
+ * leaves its last contents there (the control words are cleared at the start
+ * of each call): calls that overlap on the GPU -- on different streams, or
+ * from different host threads -- race and must not be issued.  Other
+ * arguments and errors as for mslice_forward. */
+int mslice_forward_static(const mslice_params *p, const float *vol, const float *probe,
+                          float *intensity, float *field_out, void *stream);
+
 /* Gradient of a real loss through the forward model, for a given detector
  * gradient (replaces the autograd backward of Sec. 3-4).
  *   g_psi      [nw][nz][ny] complex: dL/dRe(Psi) + i dL/dIm(Psi)

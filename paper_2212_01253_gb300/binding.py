@@ -112,6 +112,7 @@ def _load():
             sig = {
                 "mslice_workspace_size": ([P, ctypes.c_int], sz),
                 "mslice_forward": ([P, vp, vp, vp, vp, vp, sz, vp], ctypes.c_int),
+                "mslice_forward_static": ([P, vp, vp, vp, vp, vp], ctypes.c_int),
                 "mslice_adjoint": ([P, vp, vp, vp, vp, vp, sz, vp], ctypes.c_int),
                 "mslice_loss_grad": ([P, vp, vp, vp, ctypes.c_float, vp, vp, vp, vp, sz, vp],
                                      ctypes.c_int),
@@ -200,6 +201,17 @@ def mslice_forward(p, vol, probe, intensity, field_out, ws, stream=None):
         _ptr(intensity, torch.float32, nfield, "intensity"),
         _ptr(field_out, torch.complex64, nfield, "field_out"),
         _ptr(ws, torch.uint8, None, "ws"), ws.numel(), _stream(stream)), "mslice_forward")
+
+
+def mslice_forward_static(p, vol, probe, intensity, field_out, stream=None):
+    """mslice_forward with the library's fixed 32 MiB device workspace (no allocation;
+    overlapping calls race)."""
+    nvol, nfield = _sizes(p)
+    _check(_load().mslice_forward_static(
+        ctypes.byref(p), _ptr(vol, torch.complex64, nvol, "vol"),
+        _ptr(probe, torch.complex64, nfield, "probe"),
+        _ptr(intensity, torch.float32, nfield, "intensity"),
+        _ptr(field_out, torch.complex64, nfield, "field_out"), _stream(stream)), "mslice_forward_static")
 
 
 def mslice_adjoint(p, vol, probe, g_psi, grad_vol, ws, stream=None):

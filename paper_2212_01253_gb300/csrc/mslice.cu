@@ -479,6 +479,14 @@ int run_gradient(const mslice_params* p, Plan& P, bool loss, cudaStream_t st) {
     return MSLICE_OK;
 }
 
+// Allocation-free forward: the workspace is a fixed file-scope device array.
+// Host code must not use g_static_ws directly (its host-side name is a stand-in,
+// not a device address); its device address is taken once per device with
+// cudaGetSymbolAddress and cached.
+constexpr size_t kStaticWsBytes = (size_t)32 << 20;
+__device__ __align__(256) unsigned char g_static_ws[kStaticWsBytes];
+void* g_static_ws_ptr[64];
+
 }  // namespace
 
 extern "C" {
@@ -510,6 +518,22 @@ int mslice_forward(const mslice_params* p, const float* vol, const float* probe,
     if (p->flags & MSLICE_EXIT_WAVE)
         return launch_coop((const void*)k_last<C_EXIT>, P.grid, P.smem, a, st, KID_LAST, u);
     return launch_coop((const void*)k_last<C_FAR>, P.grid, P.smem, a, st, KID_LAST, u);
+}
+
+int mslice_forward_static(const mslice_params* p, const float* vol, const float* probe, float* intensity,
+                          float* field_out, void* stream) {
+    int rc = validate(p);
+    if (rc) return rc;
+    if (make_layout(p, MSLICE_OP_FORWARD).total > kStaticWsBytes) return MSLICE_EWORKSPACE;
+    int dev = 0;
+    if (note(cudaGetDevice(&dev), "cudaGetDevice")) return MSLICE_ELAUNCH;
+    if (dev < 0 || dev >= 64) return MSLICE_EUNSUPPORTED;
+    if (!g_static_ws_ptr[dev]) {
+        void* ptr = nullptr;
+        if (note(cudaGetSymbolAddress(&ptr, g_static_ws), "cudaGetSymbolAddress")) return MSLICE_ELAUNCH;
+        g_static_ws_ptr[dev] = ptr;
+    }
+    return mslice_forward(p, vol, probe, intensity, field_out, g_static_ws_ptr[dev], kStaticWsBytes, stream);
 }
 
 int mslice_adjoint(const mslice_params* p, const float* vol, const float* probe, const float* g_psi,

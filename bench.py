@@ -142,7 +142,7 @@ def measured_peaks():
         return {}
 
 
-SWEEP_SOURCES = ("mslice_device.cuh", "mslice_inst.cu", "mslice_kernels.h", "mslice.cu")
+SWEEP_SOURCES = ("mslice_device.cuh", "mslice_inst.cu", "mslice_kernels.h")
 
 
 def source_hash():
@@ -367,6 +367,115 @@ def run_gpu(args):
     return 0
 
 
+# ---------------------------------------------------------------------------
+# extra workloads (not the headline line): batched uneven jobs, reconstruction
+# ---------------------------------------------------------------------------
+def run_batch(args):
+    """64 independent structures of uneven shape (grids 128..512 per axis,
+    128..1024 slices, 0.1-0.5 deg), loss + gradient of all of them as one
+    CUDA-graph launch; voxel-slice-steps/s over the whole batch."""
+    import torch
+
+    import cssi_inputs as ci
+    from paper_2212_01253_gb300 import binding as B
+    from paper_2212_01253_gb300 import build as cuda_build
+    from paper_2212_01253_gb300.batch import BatchedLossGrad
+
+    cuda_build.build()
+    torch.cuda.set_device(0)
+    specs = ci.batched_jobs(0, args.jobs)
+    jobs = []
+    t0 = time.perf_counter()
+    for k, sp in enumerate(specs):
+        ny, nz, ns = sp["ny"], sp["nz"], sp["ns"]
+        vol = torch.from_numpy(ci.pillars_large(sp["seed"] % (1 << 20), ny=ny, nz=nz, ns=ns,
+                                                count=max(4, ny * ns // 10000))).cuda()
+        p = B.make_params(ny, nz, ns, (sp["alpha_deg"],))
+        ws = B.workspace(p, B.MSLICE_OP_FORWARD)
+        inten = torch.empty((1, nz, ny), dtype=torch.float32, device="cuda")
+        B.mslice_forward(p, vol, None, inten, None, ws)
+        del ws
+        jobs.append(dict(vol=vol, meas=torch.sqrt(inten[0] * 1.05).contiguous(), scale=1.0,
+                         alpha_deg=sp["alpha_deg"]))
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    bat = BatchedLossGrad(jobs, tune=not args.no_tune)
+    bat.capture()
+    for _ in range(args.warmup):
+        bat.replay()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        bat.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    bat.check()
+    ms = e0.elapsed_time(e1) / args.steps
+    # the same batch as eager per-group calls (no graph) for comparison
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record()
+    for _ in range(args.steps):
+        bat.run()
+    f1.record()
+    torch.cuda.synchronize()
+    line = {"metric": "batched multislice voxel-steps/s fwd+adjoint", "value": bat.units / (ms / 1e3),
+            "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "eager_ms_per_step": f0.elapsed_time(f1) / args.steps, "higher_is_better": True,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "%d structures, grids 128-512 per axis, 128-1024 slices, 0.1-0.5 deg, "
+                                   "one CUDA graph" % len(jobs),
+                       "groups": len(bat.groups), "units_per_step": bat.units, "setup_s": setup_s}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_recon(args):
+    """Reconstruction of a coarse 64^3 Au occupancy on a 256x256x512 grid from a
+    Poisson target (1e6 counts): iterations and wall time until the reduced
+    chi^2 reaches 1.1x that of the ground truth (or the iteration cap)."""
+    import torch
+
+    import cssi_inputs as ci
+    from paper_2212_01253_gb300 import binding as B
+    from paper_2212_01253_gb300 import build as cuda_build
+    from paper_2212_01253_gb300.recon import Reconstructor
+
+    cuda_build.build()
+    torch.cuda.set_device(0)
+    ny = nz = 256
+    ns = 512
+    shape, block, off = (64, 64, 64), (8, 2, 4), (0, 128, 0)
+    p = B.make_params(ny, nz, ns, (0.3,))
+    c = B.make_coarse(shape, block, off)
+    rng = np.random.default_rng(0)
+    truth = np.zeros(shape, np.float32)
+    for _ in range(16):   # 16 Au pillars in coarse space, 1-8 coarse voxels tall
+        a0, c0 = rng.integers(0, 56), rng.integers(0, 56)
+        la, lc, h = rng.integers(2, 9), rng.integers(2, 9), rng.integers(1, 9)
+        truth[a0:a0 + la, :h, c0:c0 + lc] = 4.7e-5
+    base = torch.from_numpy(ci.substrate(ny, nz, ns)).cuda()
+    vol_gt = base.clone()
+    B.mslice_coarse_to_fine(p, c, torch.from_numpy(truth.ravel()).cuda(), vol_gt)
+    ws = B.workspace(p, B.MSLICE_OP_FORWARD)
+    inten = torch.empty((1, nz, ny), dtype=torch.float32, device="cuda")
+    B.mslice_forward(p, vol_gt, None, inten, None, ws)
+    I_gt = inten.cpu().numpy().astype(np.float64)
+    meas, s = ci.poisson_target(I_gt, COUNTS, seed=0)
+    chi2_gt = 4 * ((np.sqrt(s * I_gt) - meas) ** 2).sum() / meas.size
+    R = Reconstructor(p, c, base, torch.from_numpy(meas).cuda(), s, lr=args.lr)
+    it, sec, hist = R.run(chi2_target=1.1 * chi2_gt, max_iters=args.max_iters, check_every=5)
+    line = {"metric": "reconstruction wall time to chi2_red <= 1.1 chi2_red(truth)", "value": sec, "unit": "s",
+            "higher_is_better": False, "reached": bool(hist and hist[-1][1] <= 1.1 * chi2_gt), "iterations": it,
+            "ms_per_iteration": 1e3 * sec / it, "chi2_truth": chi2_gt, "chi2_start": hist[0][1] if hist else None,
+            "chi2_end": hist[-1][1] if hist else None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "256x256 grid, 512 slices, 0.3 deg, 64^3 coarse delta (8x2x4 fine voxels each, "
+                                   "top half), Poisson target 1e6 counts, zero (bare substrate) start, ADAM lr %g"
+                                   % args.lr}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -379,11 +488,22 @@ def main():
     ap.add_argument("--cpu-angles", type=int, default=3)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="sweep", choices=["sweep", "batch", "recon"],
+                    help="sweep: the headline 512x512x1024 9-angle step; batch: 64 uneven "
+                         "structures in one graph; recon: time to a fixed chi^2")
+    ap.add_argument("--jobs", type=int, default=64)
+    ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--lr", type=float, default=2e-6)
+    ap.add_argument("--max-iters", type=int, default=300)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("at least 3 warm-up steps")
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch":
+        return run_batch(args)
+    if args.workload == "recon":
+        return run_recon(args)
     return run_gpu(args)
 
 

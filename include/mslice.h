@@ -222,6 +222,51 @@ int mslice_fine_to_coarse(const mslice_params *p, const mslice_coarse *c, const 
 int mslice_adam_step(float *theta, float *m, float *v, const float *grad, size_t n, float lr,
                      float b1, float b2, float eps, int t, float lo, float hi, void *stream);
 
+/* ------------------------------------------------------------------------
+ * Learned initialiser kernels: a small network maps the log-scaled detector
+ * image to a coarse delta volume that starts the gradient reconstruction.
+ * (The paper has no network; its reconstructions start from a guess, Sec. 4.)
+ * ------------------------------------------------------------------------ */
+
+/* Dense layer on the tensor cores: C[m][n] = beta*C[m][n] + sum_k A(m,k) B(n,k)
+ * (+ bias[n]) (ReLU if relu), A(m,k) = A[m*sam + k*sak], B(n,k) = B[n*sbn + k*sbk]
+ * (strides give transposes; sam = sak = 0 makes A a constant).  FP32 arrays,
+ * operands rounded to BF16 (nearest even), FP32 accumulation.  bias may be
+ * NULL; beta = 0 overwrites C.  Long-K shapes split K over CTAs: the partial
+ * sums go to ws (caller-owned device memory, 16-byte aligned, at least
+ * mslice_nn_gemm_workspace(M, N, K) bytes; 0 means none is needed) and are
+ * summed in a fixed order, so results are deterministic.  C must not alias A,
+ * B or ws. */
+size_t mslice_nn_gemm_workspace(int M, int N, int K);
+int mslice_nn_gemm(int M, int N, int K, const float *A, long long sam, long long sak, const float *B,
+                   long long sbn, long long sbk, float *C, long long ldc, const float *bias, int relu,
+                   float beta, void *ws, size_t ws_bytes, void *stream);
+/* Patch permutation between NHWC [B][H][W][C] and [B][H/p][W/p][p][p][C]
+ * (inverse = 0: NHWC -> patches; 1: back).  A convolution with kernel = stride
+ * = p is a GEMM on the patch layout; its transpose is a GEMM followed by the
+ * inverse permutation.  H and W must be multiples of p; in and out must not alias. */
+int mslice_nn_space_to_depth(const float *in, float *out, int B, int H, int W, int C, int p, int inverse,
+                             void *stream);
+/* ReLU backward: dz = dy where y > 0, else 0 (y = ReLU output), n elements. */
+int mslice_nn_relu_backward(const float *y, const float *dy, float *dz, size_t n, void *stream);
+/* Output layer: y = hi * sigmoid(z) [rows][cols]; with a target t, the mean
+ * squared error per row into row_loss[rows] (FP64, divided by rows*cols) and
+ * dz = dL/dz of L = mean((y - t)^2); target, dz, row_loss may be NULL. */
+int mslice_nn_sigmoid_mse(const float *z, const float *target, float *y, float *dz, double *row_loss,
+                          int rows, int cols, float hi, void *stream);
+/* Network input from detector intensities [nimg][nz][ny] (natural FFT order):
+ * per image s = counts / sum(I) (s = 1 if counts <= 0), a = sqrt(s I)
+ * (+ 0.5 noise[i] when noise, a standard normal array of the same shape, is
+ * given, clamped at 0: the spread of a Poisson amplitude), and
+ * x = gain * log(1 + a^2), written centred (fftshift) to x [nimg][nz][ny]. */
+int mslice_nn_detector_features(const float *intensity, const float *noise, float *x, int nimg, int nz,
+                                int ny, float counts, float gain, void *stream);
+/* Training volumes: out[s][i0][i1][i2] = value inside any of the
+ * boxes_per_sample boxes of sample s, else 0; boxes int32
+ * [nsamples][boxes_per_sample][6] = (lo0, hi0, lo1, hi1, lo2, hi2), half-open. */
+int mslice_nn_rasterize_boxes(const int *boxes, int boxes_per_sample, int nsamples, int d0, int d1, int d2,
+                              float value, float *out, void *stream);
+
 /* Per-kernel timing (tracing).  While enabled, every kernel launch of the
  * library is bracketed by a CUDA event pair recorded on the launching stream;
  * mslice_profile_read() waits for the recorded events and returns, per kernel

@@ -109,6 +109,7 @@ def _load():
                                    "paper_2212_01253_gb300.build.build()" % _build.LIB)
             lib = ctypes.CDLL(_build.LIB)
             P, vp, sz = ctypes.POINTER(mslice_params), ctypes.c_void_p, ctypes.c_size_t
+            ll = ctypes.c_longlong
             sig = {
                 "mslice_workspace_size": ([P, ctypes.c_int], sz),
                 "mslice_forward": ([P, vp, vp, vp, vp, vp, sz, vp], ctypes.c_int),
@@ -133,6 +134,17 @@ def _load():
                                      ctypes.c_int),
                 "mslice_profile_read": ([ctypes.POINTER(mslice_kernel_time), ctypes.c_int],
                                         ctypes.c_int),
+                "mslice_nn_gemm_workspace": ([ctypes.c_int] * 3, sz),
+                "mslice_nn_gemm": ([ctypes.c_int] * 3 + [vp, ll, ll, vp, ll, ll, vp, ll, vp, ctypes.c_int,
+                                                         ctypes.c_float, vp, sz, vp], ctypes.c_int),
+                "mslice_nn_space_to_depth": ([vp, vp] + [ctypes.c_int] * 6 + [vp], ctypes.c_int),
+                "mslice_nn_relu_backward": ([vp, vp, vp, sz, vp], ctypes.c_int),
+                "mslice_nn_sigmoid_mse": ([vp, vp, vp, vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_float, vp],
+                                          ctypes.c_int),
+                "mslice_nn_detector_features": ([vp, vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                 ctypes.c_float, ctypes.c_float, vp], ctypes.c_int),
+                "mslice_nn_rasterize_boxes": ([vp] + [ctypes.c_int] * 5 + [ctypes.c_float, vp, vp],
+                                              ctypes.c_int),
             }
             for name, (args, res) in sig.items():
                 f = getattr(lib, name)
@@ -322,3 +334,79 @@ def mslice_adam_step(theta, m, v, grad, lr, b1, b2, eps, t, lo, hi, stream=None)
         _ptr(theta, torch.float32, n, "theta"), _ptr(m, torch.float32, n, "m"),
         _ptr(v, torch.float32, n, "v"), _ptr(grad, torch.float32, n, "grad"), n, float(lr), float(b1),
         float(b2), float(eps), int(t), float(lo), float(hi), _stream(stream)), "mslice_adam_step")
+
+
+# --- learned initialiser kernels --------------------------------------------------
+
+def _span_ok(t, offsets, what):
+    """The largest element offset a strided access touches must lie inside t."""
+    if max(offsets) >= t.numel() or min(offsets) < 0:
+        raise ValueError("%s: strided access outside the tensor (%d elements)" % (what, t.numel()))
+
+
+def mslice_nn_gemm_workspace(M, N, K) -> int:
+    return int(_load().mslice_nn_gemm_workspace(int(M), int(N), int(K)))
+
+
+def mslice_nn_gemm(M, N, K, A, sam, sak, B, sbn, sbk, C, ldc, bias=None, relu=False, beta=0.0, ws=None,
+                   stream=None):
+    """C[m][n] = beta C[m][n] + sum_k A[m*sam + k*sak] B[n*sbn + k*sbk] (+ bias[n]) (ReLU);
+    BF16 operands, FP32 accumulation (tensor cores)."""
+    for t, w in ((A, "A"), (B, "B"), (C, "C"), (bias, "bias")):
+        if t is not None and (not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float32
+                              or not t.is_contiguous()):
+            raise TypeError("%s must be a contiguous float32 CUDA tensor" % w)
+    _span_ok(A, [(M - 1) * sam + (K - 1) * sak, 0], "A")
+    _span_ok(B, [(N - 1) * sbn + (K - 1) * sbk, 0], "B")
+    _span_ok(C, [(M - 1) * ldc + N - 1], "C")
+    if bias is not None and bias.numel() < N:
+        raise ValueError("bias must have N elements")
+    need = mslice_nn_gemm_workspace(M, N, K)
+    if need and (ws is None or ws.numel() * ws.element_size() < need):
+        raise ValueError("gemm %dx%dx%d needs a %d-byte workspace" % (M, N, K, need))
+    wsp = ctypes.c_void_p(ws.data_ptr()) if ws is not None else None
+    wsb = ws.numel() * ws.element_size() if ws is not None else 0
+    _check(_load().mslice_nn_gemm(
+        int(M), int(N), int(K), ctypes.c_void_p(A.data_ptr()), int(sam), int(sak), ctypes.c_void_p(B.data_ptr()),
+        int(sbn), int(sbk), ctypes.c_void_p(C.data_ptr()), int(ldc),
+        ctypes.c_void_p(bias.data_ptr()) if bias is not None else None, int(bool(relu)), float(beta), wsp, wsb,
+        _stream(stream)), "mslice_nn_gemm")
+
+
+def mslice_nn_space_to_depth(x, out, B, H, W, C, p, inverse=False, stream=None):
+    n = B * H * W * C
+    _check(_load().mslice_nn_space_to_depth(
+        _ptr(x, torch.float32, n, "in"), _ptr(out, torch.float32, n, "out"), int(B), int(H), int(W), int(C),
+        int(p), int(bool(inverse)), _stream(stream)), "mslice_nn_space_to_depth")
+
+
+def mslice_nn_relu_backward(y, dy, dz, stream=None):
+    n = y.numel()
+    _check(_load().mslice_nn_relu_backward(
+        _ptr(y, torch.float32, n, "y"), _ptr(dy, torch.float32, n, "dy"), _ptr(dz, torch.float32, n, "dz"), n,
+        _stream(stream)), "mslice_nn_relu_backward")
+
+
+def mslice_nn_sigmoid_mse(z, target, y, dz, row_loss, rows, cols, hi=1.0, stream=None):
+    n = rows * cols
+    _check(_load().mslice_nn_sigmoid_mse(
+        _ptr(z, torch.float32, n, "z"), _ptr(target, torch.float32, n, "target"), _ptr(y, torch.float32, n, "y"),
+        _ptr(dz, torch.float32, n, "dz"), _ptr(row_loss, torch.float64, rows, "row_loss"), int(rows), int(cols),
+        float(hi), _stream(stream)), "mslice_nn_sigmoid_mse")
+
+
+def mslice_nn_detector_features(intensity, noise, x, nimg, nz, ny, counts, gain=1.0, stream=None):
+    n = nimg * nz * ny
+    _check(_load().mslice_nn_detector_features(
+        _ptr(intensity, torch.float32, n, "intensity"), _ptr(noise, torch.float32, n, "noise"),
+        _ptr(x, torch.float32, n, "x"), int(nimg), int(nz), int(ny), float(counts), float(gain),
+        _stream(stream)), "mslice_nn_detector_features")
+
+
+def mslice_nn_rasterize_boxes(boxes, out, shape, value, stream=None):
+    """boxes int32 [nsamples][nboxes][6] -> out float32 [nsamples][shape]."""
+    ns_, nb_ = int(boxes.shape[0]), int(boxes.shape[1])
+    d0, d1, d2 = (int(v) for v in shape)
+    _check(_load().mslice_nn_rasterize_boxes(
+        _ptr(boxes, torch.int32, ns_ * nb_ * 6, "boxes"), nb_, ns_, d0, d1, d2, float(value),
+        _ptr(out, torch.float32, ns_ * d0 * d1 * d2, "out"), _stream(stream)), "mslice_nn_rasterize_boxes")

@@ -2,9 +2,10 @@
 
 For a grid shape (ny, nz) and a number of wavefields nw it times the forward
 slice loop over a short synthetic volume for every candidate launch shape --
-the number of persistent blocks and the column-group width of the column pass
+the number of persistent blocks, the column-group width of the column pass
 (the number of adjacent columns whose z-FFTs one group of threads runs
-together) -- and keeps the fastest.  Results are cached per device in a JSON
+together) and, for nw >= 2, the slice-loop schedule (one grid barrier per pass,
+or two wavefield groups with split-phase barriers) -- and keeps the fastest.  Results are cached per device in a JSON
 file next to the built library.  The shape changes only which threads do which
 transform, never the arithmetic, so results are bitwise independent of it.
 """
@@ -62,14 +63,15 @@ def col_widths(nz):
 
 def candidates(ny, nz, nw, sms):
     grids = sorted({0, sms, max(1, sms // 2), max(1, sms // 4)})
-    return [(g, cw) for g in grids for cw in col_widths(nz)]
+    scheds = (1, 2) if nw >= 2 else (1,)
+    return [(g, cw, sc) for g in grids for cw in col_widths(nz) for sc in scheds]
 
 
-def _time_forward(ny, nz, nw, grid, cw, ns=16, reps=3, device="cuda"):
+def _time_forward(ny, nz, nw, grid, cw, sched, ns=16, reps=3, device="cuda"):
     rng = np.random.default_rng(0)
     vol = torch.from_numpy((rng.uniform(0, 5e-5, (ns, nz, ny)) + 1j * rng.uniform(0, 5e-6, (ns, nz, ny)))
                            .astype(np.complex64)).to(device)
-    p = B.make_params(ny, nz, ns, np.linspace(0.1, 0.5, nw), grid_blocks=grid, col_width=cw)
+    p = B.make_params(ny, nz, ns, np.linspace(0.1, 0.5, nw), grid_blocks=grid, col_width=cw, schedule=sched)
     ws = B.workspace(p, B.MSLICE_OP_FORWARD, device)
     inten = torch.empty((nw, nz, ny), dtype=torch.float32, device=device)
     B.mslice_forward(p, vol, None, inten, None, ws)
@@ -88,27 +90,27 @@ def _time_forward(ny, nz, nw, grid, cw, ns=16, reps=3, device="cuda"):
 
 
 def tune(ny, nz, nw, device="cuda", force=False):
-    """(grid_blocks, col_width) for this shape, tuned on first use and cached."""
+    """(grid_blocks, col_width, schedule) for this shape, tuned on first use and cached."""
     dev = torch.device(device)
-    key = "%s|%d|%d|%d" % (torch.cuda.get_device_name(dev), ny, nz, nw)
+    key = "v2|%s|%d|%d|%d" % (torch.cuda.get_device_name(dev), ny, nz, nw)
     with _lock:
         cache = _load_cache()
         if not force and key in cache:
             return tuple(cache[key]["shape"])
         sms = torch.cuda.get_device_properties(dev).multi_processor_count
         results = []
-        for g, cw in candidates(ny, nz, nw, sms):
-            results.append((_time_forward(ny, nz, nw, g, cw, device=dev), g, cw))
+        for g, cw, sc in candidates(ny, nz, nw, sms):
+            results.append((_time_forward(ny, nz, nw, g, cw, sc, device=dev), g, cw, sc))
         results.sort()
-        ms, g, cw = results[0]
-        cache[key] = {"shape": [g, cw], "ms_16_slices": ms,
-                      "tried": [[r[1], r[2], r[0]] for r in results]}
+        ms, g, cw, sc = results[0]
+        cache[key] = {"shape": [g, cw, sc], "ms_16_slices": ms,
+                      "tried": [[r[1], r[2], r[3], r[0]] for r in results]}
         _save_cache()
-        return (g, cw)
+        return (g, cw, sc)
 
 
 def apply(p, device="cuda"):
-    """Set p.grid_blocks and p.col_width from the tuned shape of (p.ny, p.nz, p.nw)."""
-    g, cw = tune(p.ny, p.nz, p.nw, device)
-    p.grid_blocks, p.col_width = int(g), int(cw)
+    """Set p.grid_blocks, p.col_width and p.schedule from the tuned shape of (p.ny, p.nz, p.nw)."""
+    g, cw, sc = tune(p.ny, p.nz, p.nw, device)
+    p.grid_blocks, p.col_width, p.schedule = int(g), int(cw), int(sc)
     return p

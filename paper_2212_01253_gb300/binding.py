@@ -50,12 +50,13 @@ class mslice_params(ctypes.Structure):
         ("flags", ctypes.c_uint32),
         ("grid_blocks", ctypes.c_int32),
         ("col_width", ctypes.c_int32),
+        ("schedule", ctypes.c_int32),
     ]
 
 
 def make_params(ny, nz, ns, alpha_i_deg=(0.3,), wavelength_nm=0.155, slice_nm=20.0,
                 dy_nm=2.0, dz_nm=2.0, checkpoint_every=32, flags=0, psi_rad=0.0, grid_blocks=0,
-                col_width=0):
+                col_width=0, schedule=0):
     """mslice_params from plain numbers (angles in degrees)."""
     alphas = [math.radians(float(a)) for a in (alpha_i_deg if hasattr(alpha_i_deg, "__len__")
                                                else [alpha_i_deg])]
@@ -71,6 +72,7 @@ def make_params(ny, nz, ns, alpha_i_deg=(0.3,), wavelength_nm=0.155, slice_nm=20
     p.flags = int(flags)
     p.grid_blocks = int(grid_blocks)
     p.col_width = int(col_width)
+    p.schedule = int(schedule)
     return p
 
 

@@ -139,7 +139,7 @@ int validate(const mslice_params* p) {
         if (!(fabs(p->alpha_i_rad[w]) < 1.5707963)) return MSLICE_EINVAL;
     if (p->psi_rad != 0.0) return MSLICE_EUNSUPPORTED;
     if (p->flags & ~(MSLICE_EXIT_WAVE | MSLICE_PER_STRUCTURE)) return MSLICE_EINVAL;
-    if (p->grid_blocks < 0 || p->col_width < 0) return MSLICE_EINVAL;
+    if (p->grid_blocks < 0 || p->col_width < 0 || p->schedule < 0 || p->schedule > 2) return MSLICE_EINVAL;
     if (p->col_width > 0 && !col_cw_ok(p->col_width, p->nz > 32 ? p->nz / 32 : 1)) return MSLICE_EINVAL;
     return MSLICE_OK;
 }
@@ -166,7 +166,8 @@ Layout make_layout(const mslice_params* p, int op) {
     L.field = off; off = align256(off + fb);
     if (op == MSLICE_OP_ADJOINT || op == MSLICE_OP_LOSS_GRAD) {
         L.gfield = off; off = align256(off + fb);
-        L.gpart = off; off = align256(off + (p->nw > 1 && !(p->flags & MSLICE_PER_STRUCTURE) ? fb : 0));
+        L.gpart = off; off = align256(off + (p->nw > 1 && !(p->flags & MSLICE_PER_STRUCTURE)
+                                                  ? (p->schedule == 2 ? 2 : 1) * fb : 0));
         L.ckpt = off; off = align256(off + (size_t)L.nseg * fb);
         L.seg = off; off = align256(off + (size_t)L.K * fb);
     }
@@ -427,6 +428,7 @@ int prepare(const mslice_params* p, int op, const float* vol, const float* probe
     a.seg_from = 0x7fffffff;
     a.per_w = (p->flags & MSLICE_PER_STRUCTURE) ? 1 : 0;
     a.lcw = ilog2(cw);
+    a.split = p->nw >= 2 && p->schedule == 2;
     return MSLICE_OK;
 }
 

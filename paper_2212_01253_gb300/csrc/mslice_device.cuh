@@ -290,7 +290,8 @@ struct GroupSync {
     }
 };
 
-// ctrl[0] = status bits, ctrl[1] = arrivals, ctrl[2] = exits
+// ctrl[0] = status bits, ctrl[1] = arrivals, ctrl[2] = exits, ctrl[3] = arrivals
+// of the second wavefield group (split-phase schedule)
 struct Grid {
     unsigned* ctrl;
     unsigned nblocks;
@@ -328,6 +329,41 @@ struct Grid {
         __syncthreads();
         return *(volatile int*)s_ok != 0;
     }
+    // Split-phase barrier on arrival counter ctrl[slot] (slots 1 and 3): a block
+    // arrives once its writes of a phase are done and waits for the phase only
+    // when it needs the other blocks' results, doing other work in between.
+    __device__ __forceinline__ void arrive(int slot) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            red_release_add(&ctrl[slot], 1u);
+        }
+    }
+    // Wait until every block made `arrivals` arrivals on ctrl[slot]; false
+    // (uniformly per block) on timeout or an error reported by another block.
+    __device__ __forceinline__ bool wait(int slot, unsigned arrivals) {
+        if (threadIdx.x == 0) {
+            int ok = 1;
+            const unsigned target = arrivals * nblocks;
+            unsigned long long t0 = globaltimer();
+            unsigned spins = 0;
+            while ((int)(ld_acquire(&ctrl[slot]) - target) < 0) {
+                if (++spins > 64) {
+                    if (*(volatile unsigned*)&ctrl[0]) { ok = 0; break; }
+                    if ((long long)(globaltimer() - t0) > timeout_ns) {
+                        atomicOr(&ctrl[0], kStatusTimeout);
+                        ok = 0;
+                        break;
+                    }
+                    __nanosleep(32);
+                }
+            }
+            __threadfence();
+            *(volatile int*)s_ok = ok;
+        }
+        __syncthreads();
+        return *(volatile int*)s_ok != 0;
+    }
     // last block out resets the counters for the next launch on the stream
     __device__ __forceinline__ void finish() {
         __syncthreads();
@@ -336,6 +372,7 @@ struct Grid {
             const unsigned prev = atomicAdd(&ctrl[2], 1u);
             if (prev == nblocks - 1) {
                 atomicExch(&ctrl[1], 0u);
+                atomicExch(&ctrl[3], 0u);
                 atomicExch(&ctrl[2], 0u);
                 __threadfence();
             }
@@ -361,7 +398,8 @@ struct SweepArgs {
     const float2* tab;      // Wt_y[ny] | Wt_z[nz] | P_y[ny]/ny | P_z[nz]/nz
     float2* field;          // [nw][nz][ny] forward state
     float2* gfield;         // [nw][nz][ny] adjoint state
-    float2* gpart;          // [nw][nz][ny] per-wavefield gradient (nw > 1)
+    float2* gpart;          // [nw][nz][ny] per-wavefield gradient (nw > 1); [2][..] by slice
+                            // parity under the split-phase schedule
     float2* ckpt;           // [nseg][nw][nz][ny]
     float2* seg;            // [K][nw][nz][ny]  a_j of the current segment
     float2* grad;           // [ns][nz][ny]
@@ -382,6 +420,7 @@ struct SweepArgs {
     int prop_last;          // forward: the last slice of the range also propagates
     int per_w;              // 1: wavefield w has its own volume (tvol, grad: [nw][ns][nz][ny])
     int lcw;                // log2 of the columns per column-pass group
+    int split;              // 1: two wavefield groups with split-phase barriers
     float scales[MSLICE_MAX_ANGLES];  // per-wavefield loss scale when per_w
 };
 
@@ -420,20 +459,22 @@ enum : int {
 
 // ----- row pass: one team of T = ny/32 threads (1 thread for ny <= 32) per row
 template <int OP, int NC = 0>
-__device__ void row_pass(const SweepArgs& A, const Smem& S, const int j, const bool first, const bool prop) {
+__device__ void row_pass(const SweepArgs& A, const Smem& S, const int j, const bool first, const bool prop,
+                         const int w0 = 0, int wn = 0) {
+    if (wn <= 0) wn = A.nw;
     const int N = NC ? NC : A.ny, T = row_T(N), P = N > 32 ? 32 : N;
     const int tpw = 32 / T;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int tm = lane / T, t = lane % T;
     float2* reg = S.exch + (size_t)(warp * tpw + tm) * (N + N / 32);
     const size_t npx = (size_t)A.ny * A.nz;
-    const int ntasks = A.nz * A.nw;
+    const int ntasks = A.nz * wn;
     const int wtasks = (ntasks + tpw - 1) / tpw;
     const WarpSync sync;
     for (int wt = blockIdx.x * MS_WARPS + warp; wt < wtasks; wt += gridDim.x * MS_WARPS) {
         const int task = wt * tpw + tm;
         const bool active = task < ntasks;
-        const int z = active ? task / A.nw : 0, w = active ? task % A.nw : 0;
+        const int z = active ? task / wn : 0, w = w0 + (active ? task % wn : 0);
         const size_t row = (size_t)w * npx + (size_t)z * N;
         float2 x[32];
 #pragma unroll
@@ -487,7 +528,8 @@ __device__ void row_pass(const SweepArgs& A, const Smem& S, const int j, const b
                 for (int m = 0; m < 32; ++m) if (m < P) x[m] = __ldcg(A.gfield + row + t + T * m);
                 // x = g_{a_j}; gradient contribution -i kd a_j conj(g)
                 const float2* a = A.seg + (size_t)(j - A.seg_base) * A.nw * npx + row;
-                float2* gdst = (A.nw == 1 || A.per_w) ? (A.grad + vol_offset(A, w, j, z, N)) : (A.gpart + row);
+                float2* gdst = (A.nw == 1 || A.per_w) ? (A.grad + vol_offset(A, w, j, z, N))
+                                                      : (A.gpart + (size_t)(A.split & j) * A.nw * npx + row);
 #pragma unroll
                 for (int m = 0; m < 32; ++m) {
                     if (m < P) {
@@ -539,7 +581,8 @@ __host__ __device__ __forceinline__ int col_rs(int N, int cw) { return N + N / 3
 
 // ----- column pass: a group of cw*T threads per cw adjacent columns
 template <int OP, int NC = 0>
-__device__ void col_pass(const SweepArgs& A, const Smem& S, double* s_red) {
+__device__ void col_pass(const SweepArgs& A, const Smem& S, double* s_red, const int w0 = 0, int wn = 0) {
+    if (wn <= 0) wn = A.nw;
     const int N = NC ? NC : A.nz, T = row_T(N), P = N > 32 ? 32 : N;
     const int lcw = A.lcw, cw = 1 << lcw;
     const int lg = lcw + ilog2(T), gthreads = 1 << lg;
@@ -549,12 +592,12 @@ __device__ void col_pass(const SweepArgs& A, const Smem& S, double* s_red) {
     float2* reg = S.exch + (size_t)(g * cw + c) * col_rs(N, cw);
     const size_t npx = (size_t)A.ny * A.nz;
     const int ncg = (A.ny + cw - 1) / cw;
-    const int ntasks = ncg * A.nw;
+    const int ntasks = ncg * wn;
     const GroupSync sync{1 + g, gthreads};
     const float2* src = (OP == C_ADJ) ? A.gfield : (OP == C_SEED ? A.gpsi : A.field);
     double loss = 0.0;
     for (int task = blockIdx.x * groups + g; task < ntasks; task += gridDim.x * groups) {
-        const int cg = task / A.nw, w = task % A.nw;
+        const int cg = task / wn, w = w0 + task % wn;
         const int col = cg * cw + c;
         const bool active = col < A.ny;
         const size_t base = (size_t)w * npx + col;
@@ -631,14 +674,48 @@ __device__ void col_pass(const SweepArgs& A, const Smem& S, double* s_red) {
     }
 }
 
-// grad[j] = sum_w gpart[w]  (fixed order over w)
+// grad[j] = sum_w gpart[w]  (fixed order over w).  Two grid points per thread
+// step with 16-byte accesses when the sizes and the gradient pointer allow,
+// the nw loads of a step issued before their sum.
 __device__ void reduce_gpart(const SweepArgs& A, int j) {
     const size_t npx = (size_t)A.ny * A.nz;
     const size_t stride = (size_t)gridDim.x * blockDim.x;
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < npx; i += stride) {
-        float2 s = __ldcg(A.gpart + i);
-        for (int w = 1; w < A.nw; ++w) s = cadd(s, __ldcg(A.gpart + (size_t)w * npx + i));
-        __stcs(A.grad + (size_t)j * npx + i, s);
+    const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const float2* gp = A.gpart + (size_t)(A.split & j) * A.nw * npx;
+    float2* dst = A.grad + (size_t)j * npx;
+    if ((npx & 1) == 0 && ((uintptr_t)dst & 15) == 0) {
+        const size_t n4 = npx / 2;
+        const float4* g4 = reinterpret_cast<const float4*>(gp);
+        float4* d4 = reinterpret_cast<float4*>(dst);
+        for (size_t i = tid; i < n4; i += stride) {
+            float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int w0 = 0; w0 < A.nw; w0 += 8) {
+                float4 v[8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k)
+                    if (w0 + k < A.nw) v[k] = __ldcg(g4 + (size_t)(w0 + k) * n4 + i);
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    if (w0 + k < A.nw) {
+                        if (w0 + k == 0) {
+                            s = v[0];
+                        } else {
+                            s.x += v[k].x;
+                            s.y += v[k].y;
+                            s.z += v[k].z;
+                            s.w += v[k].w;
+                        }
+                    }
+                }
+            }
+            __stcs(d4 + i, s);
+        }
+        return;
+    }
+    for (size_t i = tid; i < npx; i += stride) {
+        float2 s = __ldcg(gp + i);
+        for (int w = 1; w < A.nw; ++w) s = cadd(s, __ldcg(gp + (size_t)w * npx + i));
+        __stcs(dst + i, s);
     }
 }
 
@@ -670,19 +747,56 @@ __device__ Smem load_tables(const SweepArgs& A, float2* base) {
 template <int NY, int NZ>
 __global__ void __launch_bounds__(MS_THREADS, 1) k_fwd_t(const SweepArgs A) {
     MS_KERNEL_PROLOGUE
-    const size_t slice_bytes = (size_t)A.ny * A.nz * sizeof(float2);
+    const size_t npx = (size_t)A.ny * A.nz;
+    const size_t slice_bytes = npx * sizeof(float2);
+    if (!A.split) {
+        for (int j = A.j_begin; j < A.j_end; ++j) {
+            const bool prop = (j < A.j_end - 1) || A.prop_last;
+            row_pass<R_FWD, NY>(A, S, j, j == A.j_begin, prop);
+            if (prop) {
+                if (!grid.sync()) return;
+                if (j + 1 < A.j_end) {
+                    for (int w = 0; w < (A.per_w ? A.nw : 1); ++w)
+                        prefetch_l2(A.tvol + (size_t)w * A.ns * npx * A.per_w + (size_t)(j + 1) * npx, slice_bytes);
+                }
+                col_pass<C_PROP, NZ>(A, S, s_red);
+                if (j < A.j_end - 1 && !grid.sync()) return;
+            }
+        }
+        grid.finish();
+        return;
+    }
+    // Split-phase schedule: wavefields [0, h) and [h, nw) advance in the order
+    // R0(j) R1(j) C0(j) C1(j) R0(j+1) ...; a block waits for the other blocks
+    // only where it reads their results, one half-phase after it arrived, so the
+    // barrier latency and the blocks' imbalance overlap with the other group.
+    const int h = (A.nw + 1) / 2;
+    const int gw0[2] = {0, h}, gwn[2] = {h, A.nw - h}, slot[2] = {1, 3};
+    unsigned arr[2] = {0u, 0u};
     for (int j = A.j_begin; j < A.j_end; ++j) {
         const bool prop = (j < A.j_end - 1) || A.prop_last;
-        row_pass<R_FWD, NY>(A, S, j, j == A.j_begin, prop);
-        if (prop) {
-            if (!grid.sync()) return;
-            if (j + 1 < A.j_end) {
-                const size_t npx = (size_t)A.ny * A.nz;
-                for (int w = 0; w < (A.per_w ? A.nw : 1); ++w)
-                    prefetch_l2(A.tvol + (size_t)w * A.ns * npx * A.per_w + (size_t)(j + 1) * npx, slice_bytes);
+#pragma unroll
+        for (int g = 0; g < 2; ++g) {
+            if (j > A.j_begin && !grid.wait(slot[g], arr[g])) return;   // C_g(j-1) done
+            row_pass<R_FWD, NY>(A, S, j, j == A.j_begin, prop, gw0[g], gwn[g]);
+            if (prop) {
+                grid.arrive(slot[g]);
+                ++arr[g];
             }
-            col_pass<C_PROP, NZ>(A, S, s_red);
-            if (j < A.j_end - 1 && !grid.sync()) return;
+        }
+        if (!prop) break;
+        if (j + 1 < A.j_end) {
+            for (int w = 0; w < (A.per_w ? A.nw : 1); ++w)
+                prefetch_l2(A.tvol + (size_t)w * A.ns * npx * A.per_w + (size_t)(j + 1) * npx, slice_bytes);
+        }
+#pragma unroll
+        for (int g = 0; g < 2; ++g) {
+            if (!grid.wait(slot[g], arr[g])) return;                       // R_g(j) done
+            col_pass<C_PROP, NZ>(A, S, s_red, gw0[g], gwn[g]);
+            if (j < A.j_end - 1) {
+                grid.arrive(slot[g]);
+                ++arr[g];
+            }
         }
     }
     grid.finish();
@@ -728,17 +842,54 @@ template <int NY, int NZ>
 __global__ void __launch_bounds__(MS_THREADS, 1) k_adj_t(const SweepArgs A) {
     MS_KERNEL_PROLOGUE
     const size_t npx = (size_t)A.ny * A.nz;
+    const bool reduce = A.nw > 1 && !A.per_w;
+    if (!A.split) {
+        for (int j = A.j_end - 1; j >= A.j_begin; --j) {
+            row_pass<R_ADJ, NY>(A, S, j, false, j > 0);
+            if (!grid.sync()) return;
+            if (j - 1 >= A.j_begin) {
+                for (int w = 0; w < (A.per_w ? A.nw : 1); ++w)
+                    prefetch_l2(A.tvol + (size_t)w * A.ns * npx * A.per_w + (size_t)(j - 1) * npx,
+                                npx * sizeof(float2));
+                prefetch_l2(A.seg + (size_t)(j - 1 - A.seg_base) * A.nw * npx, A.nw * npx * sizeof(float2));
+            }
+            if (j > 0) col_pass<C_ADJ, NZ>(A, S, s_red);
+            if (reduce) reduce_gpart(A, j);
+            if (j > A.j_begin && !grid.sync()) return;
+        }
+        grid.finish();
+        return;
+    }
+    // Split-phase schedule as in k_fwd_t.  The gradient partials of slice j are
+    // summed after R_1(j) is complete everywhere (which implies R_0(j): every
+    // block arrives for R_1(j) after its own R_0(j)); they are double-buffered
+    // by slice parity because R_0(j-1) may start before every block has read them.
+    const int h = (A.nw + 1) / 2;
+    const int gw0[2] = {0, h}, gwn[2] = {h, A.nw - h}, slot[2] = {1, 3};
+    unsigned arr[2] = {0u, 0u};
     for (int j = A.j_end - 1; j >= A.j_begin; --j) {
-        row_pass<R_ADJ, NY>(A, S, j, false, j > 0);
-        if (!grid.sync()) return;
+#pragma unroll
+        for (int g = 0; g < 2; ++g) {
+            if (j < A.j_end - 1 && !grid.wait(slot[g], arr[g])) return;   // C_g(j+1) done
+            row_pass<R_ADJ, NY>(A, S, j, false, j > 0, gw0[g], gwn[g]);
+            grid.arrive(slot[g]);
+            ++arr[g];
+        }
         if (j - 1 >= A.j_begin) {
             for (int w = 0; w < (A.per_w ? A.nw : 1); ++w)
                 prefetch_l2(A.tvol + (size_t)w * A.ns * npx * A.per_w + (size_t)(j - 1) * npx, npx * sizeof(float2));
             prefetch_l2(A.seg + (size_t)(j - 1 - A.seg_base) * A.nw * npx, A.nw * npx * sizeof(float2));
         }
-        if (j > 0) col_pass<C_ADJ, NZ>(A, S, s_red);
-        if (A.nw > 1 && !A.per_w) reduce_gpart(A, j);
-        if (j > A.j_begin && !grid.sync()) return;
+#pragma unroll
+        for (int g = 0; g < 2; ++g) {
+            if (!grid.wait(slot[g], arr[g])) return;                        // R_g(j) done
+            if (j > 0) col_pass<C_ADJ, NZ>(A, S, s_red, gw0[g], gwn[g]);
+            if (g == 1 && reduce) reduce_gpart(A, j);
+            if (j > A.j_begin) {
+                grid.arrive(slot[g]);
+                ++arr[g];
+            }
+        }
     }
     grid.finish();
 }

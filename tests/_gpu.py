@@ -5,17 +5,17 @@ import torch
 from paper_2212_01253_gb300 import binding as B
 
 
-def params(geo, checkpoint_every=32, flags=0):
+def params(geo, checkpoint_every=32, flags=0, schedule=0):
     return B.make_params(geo.ny, geo.nz, geo.ns, np.rad2deg(geo.alpha_i_rad), geo.wavelength_nm,
-                         geo.slice_nm, geo.dy_nm, geo.dz_nm, checkpoint_every, flags)
+                         geo.slice_nm, geo.dy_nm, geo.dz_nm, checkpoint_every, flags, schedule=schedule)
 
 
 def dev(a, dtype):
     return torch.from_numpy(np.ascontiguousarray(a).astype(dtype)).cuda()
 
 
-def forward(geo, vol, probe=None, exit_wave=False, return_field=False):
-    p = params(geo, flags=B.MSLICE_EXIT_WAVE if exit_wave else 0)
+def forward(geo, vol, probe=None, exit_wave=False, return_field=False, schedule=0):
+    p = params(geo, flags=B.MSLICE_EXIT_WAVE if exit_wave else 0, schedule=schedule)
     ws = B.workspace(p, B.MSLICE_OP_FORWARD)
     v = dev(vol, np.complex64)
     pr = None if probe is None else dev(probe, np.complex64)
@@ -29,8 +29,8 @@ def forward(geo, vol, probe=None, exit_wave=False, return_field=False):
     return (I.cpu().numpy(), F.cpu().numpy()) if return_field else I.cpu().numpy()
 
 
-def loss_grad(geo, vol, meas, scale, probe=None, checkpoint_every=32, return_intensity=False):
-    p = params(geo, checkpoint_every)
+def loss_grad(geo, vol, meas, scale, probe=None, checkpoint_every=32, return_intensity=False, schedule=0):
+    p = params(geo, checkpoint_every, schedule=schedule)
     ws = B.workspace(p, B.MSLICE_OP_LOSS_GRAD)
     v = dev(vol, np.complex64)
     pr = None if probe is None else dev(probe, np.complex64)

@@ -170,6 +170,23 @@ def test_checkpoint_interval_does_not_change_the_gradient():
         assert np.array_equal(g, ref[1])
 
 
+@pytest.mark.parametrize("ny,nz,ns,nw,K", [(64, 64, 24, 2, 5), (128, 64, 17, 3, 4), (512, 512, 40, 9, 32),
+                                           (32, 32, 9, 5, 2)])
+def test_split_phase_schedule_is_bitwise_identical(ny, nz, ns, nw, K):
+    """Schedule 2 (two wavefield groups, split-phase barriers) reorders only
+    which blocks run which rows and columns when: every value is computed by
+    the same arithmetic, so intensities, loss and gradient equal schedule 1's."""
+    geo = oracle.Geometry(ny, nz, ns, alpha_i_deg=np.linspace(0.1, 0.5, nw))
+    vol = ci.random_volume(ny + ns + nw, ny, nz, ns, scale=40)
+    I1 = G.forward(geo, vol, schedule=1)
+    I2 = G.forward(geo, vol, schedule=2)
+    assert np.array_equal(I1, I2)
+    meas = (np.sqrt(I1) * 1.05).astype(np.float32)
+    L1, g1, J1 = G.loss_grad(geo, vol, meas, 0.9, checkpoint_every=K, return_intensity=True, schedule=1)
+    L2, g2, J2 = G.loss_grad(geo, vol, meas, 0.9, checkpoint_every=K, return_intensity=True, schedule=2)
+    assert L1 == L2 and np.array_equal(g1, g2) and np.array_equal(J1, J2)
+
+
 def test_adjoint_vs_oracle():
     geo = oracle.Geometry(64, 32, 10, alpha_i_deg=(0.2, 0.35))
     vol = ci.random_volume(31, 64, 32, 10, scale=40)

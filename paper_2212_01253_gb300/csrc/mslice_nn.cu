@@ -14,16 +14,121 @@ namespace {
 constexpr int kTM = 64, kTN = 64, kTK = 32;  // block tile (rows of C, columns of C, k step)
 constexpr int kPad = 8;                      // bf16 padding per smem row (16 bytes)
 
-// float -> bf16, round to nearest even (finite inputs)
-__device__ __forceinline__ uint16_t to_bf16(float x) {
-    const uint32_t a = __float_as_uint(x);
-    return (uint16_t)((a + 0x7fffu + ((a >> 16) & 1u)) >> 16);
+// two floats -> packed bf16x2 (lo in the low half), round to nearest even
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+    uint32_t d;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+    return d;
+}
+__device__ __forceinline__ uint16_t to_bf16(float x) { return (uint16_t)(pack_bf16x2(x, 0.f) & 0xffffu); }
+
+// How an operand tile (64 rows x 32 k) is read from global memory:
+// K4: k is the unit-stride index (16-byte loads along k); R4: the row index is
+// (16-byte loads along rows); SCALAR: anything else (one float per load).
+enum : int { LD_SCALAR = 0, LD_K4 = 1, LD_R4 = 2 };
+
+struct TileSrc {
+    const float* p;
+    long long srow, sk;
+    int rows;      // valid rows (M or N)
+    int mode;
+};
+
+__device__ __forceinline__ int tile_mode(const float* p, long long srow, long long sk) {
+    const bool al = ((uintptr_t)p & 15) == 0;
+    if (al && sk == 1 && (srow & 3) == 0) return LD_K4;
+    if (al && srow == 1 && (sk & 3) == 0) return LD_R4;
+    return LD_SCALAR;
+}
+
+// Each of the 128 threads holds 16 floats of the next tile.
+struct TileRegs {
+    float v[16];
+};
+
+__device__ __forceinline__ void tile_load(TileRegs& R, const TileSrc& S, int row0, int k0, int kend) {
+    const int tid = threadIdx.x;
+    if (S.mode == LD_K4) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int e = tid + 128 * q, r = e >> 3, c = (e & 7) * 4;
+            const int row = row0 + r, k = k0 + c;
+            if (row < S.rows && k + 3 < kend) {
+                const float4 f = __ldg(reinterpret_cast<const float4*>(S.p + (long long)row * S.srow + k));
+                R.v[4 * q] = f.x; R.v[4 * q + 1] = f.y; R.v[4 * q + 2] = f.z; R.v[4 * q + 3] = f.w;
+            } else {
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                    R.v[4 * q + i] = (row < S.rows && k + i < kend) ? __ldg(S.p + (long long)row * S.srow + k + i) : 0.f;
+            }
+        }
+    } else if (S.mode == LD_R4) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int e = tid + 128 * q, c = e >> 4, r = (e & 15) * 4;
+            const int row = row0 + r, k = k0 + c;
+            if (row + 3 < S.rows && k < kend) {
+                const float4 f = __ldg(reinterpret_cast<const float4*>(S.p + row + (long long)k * S.sk));
+                R.v[4 * q] = f.x; R.v[4 * q + 1] = f.y; R.v[4 * q + 2] = f.z; R.v[4 * q + 3] = f.w;
+            } else {
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                    R.v[4 * q + i] = (row + i < S.rows && k < kend) ? __ldg(S.p + row + i + (long long)k * S.sk) : 0.f;
+            }
+        }
+    } else {
+        const bool kfast = S.sk == 1;
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            const int e = tid + 128 * q;
+            const int r = kfast ? e / kTK : e % kTM, c = kfast ? e % kTK : e / kTM;
+            const int row = row0 + r, k = k0 + c;
+            R.v[q] = (row < S.rows && k < kend) ? S.p[(long long)row * S.srow + (long long)k * S.sk] : 0.f;
+        }
+    }
+}
+
+__device__ __forceinline__ void tile_store(uint16_t (*sm)[kTK + kPad], const TileRegs& R, int mode, bool kfast) {
+    const int tid = threadIdx.x;
+    if (mode == LD_K4) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int e = tid + 128 * q, r = e >> 3, c = (e & 7) * 4;
+            uint2 w;
+            w.x = pack_bf16x2(R.v[4 * q], R.v[4 * q + 1]);
+            w.y = pack_bf16x2(R.v[4 * q + 2], R.v[4 * q + 3]);
+            *reinterpret_cast<uint2*>(&sm[r][c]) = w;
+        }
+    } else if (mode == LD_R4) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int e = tid + 128 * q, c = e >> 4, r = (e & 15) * 4;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) sm[r + i][c] = to_bf16(R.v[4 * q + i]);
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            const int e = tid + 128 * q;
+            const int r = kfast ? e / kTK : e % kTM, c = kfast ? e % kTK : e / kTM;
+            sm[r][c] = to_bf16(R.v[q]);
+        }
+    }
+}
+
+__device__ __forceinline__ void ldmatrix_x4(uint32_t (&d)[4], const void* smem_row) {
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(smem_row);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(d[0]), "=r"(d[1]), "=r"(d[2]), "=r"(d[3])
+                 : "r"(a));
 }
 
 // C[m][n] = sum_k A(m, k) B(n, k) (+ bias[n]) (ReLU if relu), A(m,k) = A[m*sam + k*sak],
-// B(n,k) = B[n*sbn + k*sbk]; operands rounded to BF16, FP32 accumulation.
-// Split-K: blockIdx.z takes k in [z*kchunk, (z+1)*kchunk); with part != NULL the
-// raw partial sums go to part[z][M][N] and k_splitk_reduce finishes them.
+// B(n,k) = B[n*sbn + k*sbk]; operands rounded to BF16, FP32 accumulation
+// (mma.sync m16n8k16).  The next k-tile is read into registers while the
+// tensor cores work on the current one.  Split-K: blockIdx.z takes k in
+// [z*kchunk, (z+1)*kchunk); with part != NULL the raw partial sums go to
+// part[z][M][N] and k_splitk_reduce finishes them.
 __global__ void __launch_bounds__(128) k_gemm(int M, int N, int K, const float* __restrict__ A, long long sam,
                                               long long sak, const float* __restrict__ Bm, long long sbn,
                                               long long sbk, float* __restrict__ C, long long ldc,
@@ -37,8 +142,8 @@ __global__ void __launch_bounds__(128) k_gemm(int M, int N, int K, const float* 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;  // 2x2 warps of 32x32
     const int g = lane >> 2, tq = lane & 3;
-    // staging order: the unit-stride index runs across neighbouring threads
-    const bool a_kfast = sak == 1, b_kfast = sbk == 1;
+    const TileSrc SA{A, sam, sak, M, tile_mode(A, sam, sak)};
+    const TileSrc SB{Bm, sbn, sbk, N, tile_mode(Bm, sbn, sbk)};
     float acc[2][4][4];
 #pragma unroll
     for (int i = 0; i < 2; ++i)
@@ -46,34 +151,35 @@ __global__ void __launch_bounds__(128) k_gemm(int M, int N, int K, const float* 
         for (int j = 0; j < 4; ++j)
 #pragma unroll
             for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.f;
+    TileRegs ra, rb;
+    tile_load(ra, SA, m0, kbeg, kend);
+    tile_load(rb, SB, n0, kbeg, kend);
+    tile_store(sA, ra, SA.mode, sak == 1);
+    tile_store(sB, rb, SB.mode, sbk == 1);
+    __syncthreads();
+    // ldmatrix row addresses: A rows wm + 16 i + (lane % 16), k offset 8 (lane / 16);
+    // B rows (n) wn + 8 (2 jj + lane / 16) + lane % 8, k offset 8 ((lane / 8) % 2)
+    const int ar = lane & 15, ak = (lane >> 4) * 8;
+    const int bn = ((lane >> 4) * 8) + (lane & 7), bk = ((lane >> 3) & 1) * 8;
     for (int k0 = kbeg; k0 < kend; k0 += kTK) {
-        for (int e = threadIdx.x; e < kTM * kTK; e += blockDim.x) {
-            const int r = a_kfast ? e / kTK : e % kTM, c = a_kfast ? e % kTK : e / kTM;
-            const int m = m0 + r, k = k0 + c;
-            sA[r][c] = to_bf16((m < M && k < kend) ? A[(long long)m * sam + (long long)k * sak] : 0.f);
+        const bool more = k0 + kTK < kend;
+        if (more) {
+            tile_load(ra, SA, m0, k0 + kTK, kend);
+            tile_load(rb, SB, n0, k0 + kTK, kend);
         }
-        for (int e = threadIdx.x; e < kTN * kTK; e += blockDim.x) {
-            const int r = b_kfast ? e / kTK : e % kTN, c = b_kfast ? e % kTK : e / kTN;
-            const int n = n0 + r, k = k0 + c;
-            sB[r][c] = to_bf16((n < N && k < kend) ? Bm[(long long)n * sbn + (long long)k * sbk] : 0.f);
-        }
-        __syncthreads();
 #pragma unroll
         for (int kk = 0; kk < kTK; kk += 16) {
             uint32_t af[2][4], bf[4][2];
 #pragma unroll
-            for (int i = 0; i < 2; ++i) {
-                const int r = wm + 16 * i + g;
-                af[i][0] = *reinterpret_cast<const uint32_t*>(&sA[r][kk + 2 * tq]);
-                af[i][1] = *reinterpret_cast<const uint32_t*>(&sA[r + 8][kk + 2 * tq]);
-                af[i][2] = *reinterpret_cast<const uint32_t*>(&sA[r][kk + 2 * tq + 8]);
-                af[i][3] = *reinterpret_cast<const uint32_t*>(&sA[r + 8][kk + 2 * tq + 8]);
-            }
+            for (int i = 0; i < 2; ++i) ldmatrix_x4(af[i], &sA[wm + 16 * i + ar][kk + ak]);
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int c = wn + 8 * j + g;
-                bf[j][0] = *reinterpret_cast<const uint32_t*>(&sB[c][kk + 2 * tq]);
-                bf[j][1] = *reinterpret_cast<const uint32_t*>(&sB[c][kk + 2 * tq + 8]);
+            for (int jj = 0; jj < 2; ++jj) {
+                uint32_t t[4];
+                ldmatrix_x4(t, &sB[wn + 16 * jj + bn][kk + bk]);
+                bf[2 * jj][0] = t[0];
+                bf[2 * jj][1] = t[1];
+                bf[2 * jj + 1][0] = t[2];
+                bf[2 * jj + 1][1] = t[3];
             }
 #pragma unroll
             for (int i = 0; i < 2; ++i)
@@ -87,6 +193,11 @@ __global__ void __launch_bounds__(128) k_gemm(int M, int N, int K, const float* 
                           "r"(bf[j][1]));
         }
         __syncthreads();
+        if (more) {
+            tile_store(sA, ra, SA.mode, sak == 1);
+            tile_store(sB, rb, SB.mode, sbk == 1);
+            __syncthreads();
+        }
     }
 #pragma unroll
     for (int i = 0; i < 2; ++i)

@@ -457,6 +457,10 @@ enum : int {
     C_SEED = 5,      // F_z^H g_psi                                     gpsi -> gfield
 };
 
+#ifndef MS_ADJ_CHUNK
+#define MS_ADJ_CHUNK 16  // a_j values loaded ahead of their gradient stores
+#endif
+
 // ----- row pass: one team of T = ny/32 threads (1 thread for ny <= 32) per row
 template <int OP, int NC = 0>
 __device__ void row_pass(const SweepArgs& A, const Smem& S, const int j, const bool first, const bool prop,
@@ -526,17 +530,26 @@ __device__ void row_pass(const SweepArgs& A, const Smem& S, const int j, const b
             if (active) {
 #pragma unroll
                 for (int m = 0; m < 32; ++m) if (m < P) x[m] = __ldcg(A.gfield + row + t + T * m);
-                // x = g_{a_j}; gradient contribution -i kd a_j conj(g)
+                // x = g_{a_j}; gradient contribution -i kd a_j conj(g).  The loads of
+                // a chunk of a_j are all issued before the chunk's gradient stores (the
+                // compiler may not move a load across a store it cannot prove disjoint).
                 const float2* a = A.seg + (size_t)(j - A.seg_base) * A.nw * npx + row;
                 float2* gdst = (A.nw == 1 || A.per_w) ? (A.grad + vol_offset(A, w, j, z, N))
                                                       : (A.gpart + (size_t)(A.split & j) * A.nw * npx + row);
 #pragma unroll
-                for (int m = 0; m < 32; ++m) {
-                    if (m < P) {
-                        const float2 av = __ldcg(a + t + T * m), g = x[m];
-                        const float re = fmaf(av.x, g.x, av.y * g.y);   // Re(a conj g)
-                        const float im = fmaf(av.y, g.x, -av.x * g.y);  // Im(a conj g)
-                        __stcg(gdst + t + T * m, make_float2(A.kd * im, -A.kd * re));
+                for (int c = 0; c < 32; c += MS_ADJ_CHUNK) {
+                    float2 av[MS_ADJ_CHUNK];
+#pragma unroll
+                    for (int k = 0; k < MS_ADJ_CHUNK; ++k)
+                        if (c + k < P) av[k] = __ldcg(a + t + T * (c + k));
+#pragma unroll
+                    for (int k = 0; k < MS_ADJ_CHUNK; ++k) {
+                        if (c + k < P) {
+                            const float2 g = x[c + k];
+                            const float re = fmaf(av[k].x, g.x, av[k].y * g.y);   // Re(a conj g)
+                            const float im = fmaf(av[k].y, g.x, -av[k].x * g.y);  // Im(a conj g)
+                            __stcg(gdst + t + T * (c + k), make_float2(A.kd * im, -A.kd * re));
+                        }
                     }
                 }
                 if (prop) {
@@ -687,28 +700,35 @@ __device__ void reduce_gpart(const SweepArgs& A, int j) {
         const size_t n4 = npx / 2;
         const float4* g4 = reinterpret_cast<const float4*>(gp);
         float4* d4 = reinterpret_cast<float4*>(dst);
-        for (size_t i = tid; i < n4; i += stride) {
-            float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
-            for (int w0 = 0; w0 < A.nw; w0 += 8) {
-                float4 v[8];
+        // two grid points per thread and step: all loads of both before either store
+        for (size_t i = tid; i < n4; i += 2 * stride) {
+            const size_t i2 = i + stride;
+            const bool has2 = i2 < n4;
+            float4 s1 = make_float4(0.f, 0.f, 0.f, 0.f), s2 = s1;
+            for (int w0 = 0; w0 < A.nw; w0 += 4) {
+                float4 v1[4], v2[4];
 #pragma unroll
-                for (int k = 0; k < 8; ++k)
-                    if (w0 + k < A.nw) v[k] = __ldcg(g4 + (size_t)(w0 + k) * n4 + i);
+                for (int k = 0; k < 4; ++k) {
+                    if (w0 + k < A.nw) {
+                        v1[k] = __ldcg(g4 + (size_t)(w0 + k) * n4 + i);
+                        if (has2) v2[k] = __ldcg(g4 + (size_t)(w0 + k) * n4 + i2);
+                    }
+                }
 #pragma unroll
-                for (int k = 0; k < 8; ++k) {
+                for (int k = 0; k < 4; ++k) {
                     if (w0 + k < A.nw) {
                         if (w0 + k == 0) {
-                            s = v[0];
+                            s1 = v1[0];
+                            s2 = v2[0];
                         } else {
-                            s.x += v[k].x;
-                            s.y += v[k].y;
-                            s.z += v[k].z;
-                            s.w += v[k].w;
+                            s1.x += v1[k].x; s1.y += v1[k].y; s1.z += v1[k].z; s1.w += v1[k].w;
+                            s2.x += v2[k].x; s2.y += v2[k].y; s2.z += v2[k].z; s2.w += v2[k].w;
                         }
                     }
                 }
             }
-            __stcs(d4 + i, s);
+            __stcs(d4 + i, s1);
+            if (has2) __stcs(d4 + i2, s2);
         }
         return;
     }

@@ -54,7 +54,7 @@ def col_widths(nz):
     """Usable column-group widths for a column length nz (mirrors the library's check)."""
     T = nz // 32 if nz > 32 else 1
     out = []
-    for cw in (4, 8, 16, 32):
+    for cw in (2, 4, 8, 16, 32):
         lo = 4 if 32 // T > 4 else 32 // T
         if cw * T <= MS_THREADS and MS_THREADS % (cw * T) == 0 and cw >= lo and (T > 1 or cw == 32):
             out.append(cw)

@@ -265,7 +265,7 @@ __global__ void k_relu_back(const float* __restrict__ y, const float* __restrict
 }
 
 // y = hi * sigmoid(z); loss partial = sum (y - t)^2 / n_out per row; dz = dL/dz
-__global__ void k_sigmoid_mse(const float* __restrict__ z, const float* __restrict__ t, float* __restrict__ y,
+__global__ void __launch_bounds__(1024) k_sigmoid_mse(const float* __restrict__ z, const float* __restrict__ t, float* __restrict__ y,
                               float* __restrict__ dz, double* __restrict__ row_loss, int rows, int cols, float hi) {
     const int r = blockIdx.x;
     if (r >= rows) return;
@@ -414,7 +414,7 @@ int mslice_nn_relu_backward(const float* y, const float* dy, float* dz, size_t n
 int mslice_nn_sigmoid_mse(const float* z, const float* target, float* y, float* dz, double* row_loss, int rows,
                           int cols, float hi, void* stream) {
     if (!z || !y || rows < 1 || cols < 1) return MSLICE_EINVAL;
-    k_sigmoid_mse<<<rows, 256, 0, (cudaStream_t)stream>>>(z, target, y, dz, row_loss, rows, cols, hi);
+    k_sigmoid_mse<<<rows, 1024, 0, (cudaStream_t)stream>>>(z, target, y, dz, row_loss, rows, cols, hi);
     return cudaGetLastError() == cudaSuccess ? MSLICE_OK : MSLICE_ELAUNCH;
 }
 

@@ -19,16 +19,19 @@ bool bad_coarse(const mslice_params* p, const mslice_coarse* c) {
     return p->ny < 1 || p->nz < 1 || p->ns < 1;
 }
 
-// one thread per fine voxel of the block
+// one block per fine row (x, z) of the coarse block at a time, threads along y
 __global__ void k_coarse_to_fine(const float* __restrict__ theta, float2* __restrict__ vol, mslice_coarse c,
                                  int ny, int nz) {
-    const long bxs = (long)c.cx * c.bx, bzs = (long)c.cz * c.bz, bys = (long)c.cy * c.by;
-    const long n = bxs * bzs * bys;
-    const long stride = (long)gridDim.x * blockDim.x;
-    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const long yy = i % bys, zz = (i / bys) % bzs, xx = i / (bys * bzs);
-        const float d = theta[((xx / c.bx) * c.cz + zz / c.bz) * c.cy + yy / c.by];
-        vol[((size_t)(c.x0 + xx) * nz + (c.z0 + zz)) * ny + (c.y0 + yy)] = make_float2(d, c.beta_ratio * d);
+    const int bzs = c.cz * c.bz, bys = c.cy * c.by;
+    const long rows = (long)c.cx * c.bx * bzs;
+    for (long r = blockIdx.x; r < rows; r += gridDim.x) {
+        const int xx = (int)(r / bzs), zz = (int)(r % bzs);
+        const float* th = theta + ((size_t)(xx / c.bx) * c.cz + zz / c.bz) * c.cy;
+        float2* out = vol + ((size_t)(c.x0 + xx) * nz + (c.z0 + zz)) * ny + c.y0;
+        for (int yy = threadIdx.x; yy < bys; yy += blockDim.x) {
+            const float d = __ldg(th + yy / c.by);
+            out[yy] = make_float2(d, c.beta_ratio * d);
+        }
     }
 }
 
@@ -80,8 +83,9 @@ extern "C" {
 int mslice_coarse_to_fine(const mslice_params* p, const mslice_coarse* c, const float* theta, float* vol,
                           void* stream) {
     if (bad_coarse(p, c) || !theta || !vol) return MSLICE_EINVAL;
-    const size_t n = (size_t)c->cx * c->bx * c->cz * c->bz * c->cy * c->by;
-    k_coarse_to_fine<<<blocks_for(n), 256, 0, (cudaStream_t)stream>>>(theta, (float2*)vol, *c, p->ny, p->nz);
+    const size_t rows = (size_t)c->cx * c->bx * c->cz * c->bz;
+    const unsigned nb = (unsigned)(rows < 8192 ? rows : 8192);
+    k_coarse_to_fine<<<nb, 256, 0, (cudaStream_t)stream>>>(theta, (float2*)vol, *c, p->ny, p->nz);
     return cudaGetLastError() == cudaSuccess ? MSLICE_OK : MSLICE_ELAUNCH;
 }
 

@@ -44,13 +44,29 @@ METRIC = "multislice voxel-steps/s fwd+adjoint"
 UNIT = "voxel-slice-steps/s"
 
 
-def config(nw=NW, ns=NS):
+def config(nw=NW, ns=NS, ckpt=CKPT):
     return {
         "workload": "512x512 grid (2 nm), %d slices of 20 nm, %d incidence angles 0.10-0.50 deg, "
-                    "Si + 50 Au pillars/lines, loss + gradient (checkpoint every %d)" % (ns, nw, CKPT),
+                    "Si + 50 Au pillars/lines, loss + gradient (checkpoint every %d slices%s)"
+                    % (ns, nw, ckpt, ": every a_j kept, no recompute" if ckpt >= ns else ""),
         "grid": [NY, NZ], "slices": ns, "angles": nw, "wavelength_nm": LAM,
         "l2": "inputs larger than L2: the 2 GiB volume and 2 GiB transmission stream from HBM every pass",
     }
+
+
+def checkpoint_interval(args, ny, nz, ns, nw, dev):
+    """Adjoint checkpoint interval: --checkpoint if given, else every a_j kept
+    (one segment, no recompute) when that workspace fits in half of the
+    device's memory, else every 32 slices."""
+    import torch
+
+    from paper_2212_01253_gb300 import binding as B
+    if args.checkpoint > 0:
+        return args.checkpoint
+    total = torch.cuda.get_device_properties(dev).total_memory
+    need = B.mslice_workspace_size(B.make_params(ny, nz, ns, angles(nw), checkpoint_every=ns),
+                                   B.MSLICE_OP_LOSS_GRAD)
+    return ns if need + 4 * ny * nz * ns * 8 <= total // 2 else CKPT
 
 
 def angles(nw=NW):
@@ -232,7 +248,13 @@ def run_gpu(args):
         dist.barrier()
     dev = torch.device("cuda", local)
     nw, ns = args.angles, args.slices
-    p = B.make_params(NY, NZ, ns, angles(nw), LAM, SLICE, DY, DZ, CKPT)
+    ckpt = checkpoint_interval(args, NY, NZ, ns, nw, dev)
+    p = B.make_params(NY, NZ, ns, angles(nw), LAM, SLICE, DY, DZ, ckpt)
+    if not args.no_tune:
+        # launch shape (blocks, column-group width, schedule) from the autotuner,
+        # tuned once per device and shape outside the timed region, cached on disk
+        from paper_2212_01253_gb300 import autotune
+        autotune.apply(p, dev)
 
     # inputs: volume (seed = rank) and Poisson targets of a ground-truth volume
     vol_h = ci.pillars_large(rank, ns=ns)
@@ -358,7 +380,9 @@ def run_gpu(args):
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config(nw, ns),
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": dict(config(nw, ns, ckpt), launch_shape={"grid_blocks": p.grid_blocks, "col_width": p.col_width,
+                                                         "schedule": p.schedule}),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
             "gpu_launches": gpu_launches, "kernels": kernels, "loss": float(loss.item())}
     print(json.dumps(line), flush=True)
@@ -446,7 +470,7 @@ def run_recon(args):
     ny = nz = 256
     ns = 512
     shape, block, off = (64, 64, 64), (8, 2, 4), (0, 128, 0)
-    p = B.make_params(ny, nz, ns, (0.3,))
+    p = B.make_params(ny, nz, ns, (0.3,), checkpoint_every=ns)   # every a_j kept (268 MB)
     c = B.make_coarse(shape, block, off)
     rng = np.random.default_rng(0)
     truth = np.zeros(shape, np.float32)
@@ -518,16 +542,17 @@ def run_learned(args):
     ny = nz = 256
     ns = 512
     shape, block, off = (64, 64, 64), (8, 2, 4), (0, 128, 0)
-    p = B.make_params(ny, nz, ns, (0.3,))
+    p = B.make_params(ny, nz, ns, (0.3,), checkpoint_every=ns)   # every a_j kept (268 MB)
     c = B.make_coarse(shape, block, off)
     base = torch.from_numpy(ci.substrate(ny, nz, ns)).cuda()
     batch = 64
-    sampler = PillarSampler(p, c, base, n_pillars=(4, 16), foot=(2, 9), height=(1, 9), chunk=args.chunk)
+    sampler = PillarSampler(p, c, base, n_pillars=(4, 16), foot=(2, 9), height=(1, 9), chunk=args.chunk,
+                            tune=not args.no_tune)
     net = EncoderDecoder(ARCH_256, batch)
 
     # mean occupancy of the training distribution (the constant start)
     _, occ0, _ = sampler.sample(np.random.default_rng(999), 256, noise=False)
-    occ_mean = float(occ0.mean())
+    occ_mean = float(occ0.cpu().numpy().mean())
 
     clocks = Clocks(0)
     clocks.start()
@@ -635,6 +660,8 @@ def main():
     ap.add_argument("--train-samples", type=int, default=100000)
     ap.add_argument("--heldout", type=int, default=10)
     ap.add_argument("--chunk", type=int, default=64, help="learned: structures per forward launch")
+    ap.add_argument("--checkpoint", type=int, default=0,
+                    help="adjoint checkpoint interval (0: keep every a_j when it fits in half the HBM, else 32)")
     ap.add_argument("--jobs", type=int, default=64)
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--lr", type=float, default=2e-6)

@@ -258,10 +258,12 @@ int mslice_nn_relu_backward(const float *y, const float *dy, float *dz, size_t n
  * dz = dL/dz of L = mean((y - t)^2); target, dz, row_loss may be NULL. */
 int mslice_nn_sigmoid_mse(const float *z, const float *target, float *y, float *dz, double *row_loss,
                           int rows, int cols, float hi, void *stream);
-/* Network input from detector intensities [nimg][nz][ny] (natural FFT order):
- * per image s = counts / sum(I) (s = 1 if counts <= 0), a = sqrt(s I)
- * (+ 0.5 noise[i] when noise, a standard normal array of the same shape, is
- * given, clamped at 0: the spread of a Poisson amplitude), and
+/* Network input from detector images [nimg][nz][ny] (natural FFT order):
+ * counts > 0: intensities, a = sqrt(s I) with s = counts / sum(I) per image;
+ * counts == 0: intensities already in photon counts, a = sqrt(I);
+ * counts < 0: the input is the amplitude a itself (e.g. sqrt of measured counts).
+ * Then a += 0.5 noise[i] when noise (a standard normal array of the same shape)
+ * is given, clamped at 0 (the spread of a Poisson amplitude), and
  * x = gain * log(1 + a^2), written centred (fftshift) to x [nimg][nz][ny]. */
 int mslice_nn_detector_features(const float *intensity, const float *noise, float *x, int nimg, int nz,
                                 int ny, float counts, float gain, void *stream);

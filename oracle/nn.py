@@ -71,13 +71,17 @@ def depth_to_space(y, p):
 
 def detector_features(intensity, noise=None, counts=1e6, gain=1.0):
     """x = gain log(1 + a^2) with a = sqrt(s I) (+ 0.5 noise, clamped at 0),
-    s = counts / sum(I) per image (s = 1 for counts <= 0), centred with
-    fftshift.  intensity [nimg][nz][ny]."""
+    s = counts / sum(I) per image (s = 1 for counts == 0; for counts < 0 the
+    input is the amplitude a itself), centred with fftshift.
+    intensity [nimg][nz][ny]."""
     I = np.asarray(intensity, np.float64)
     out = np.empty_like(I)
     for i in range(I.shape[0]):
-        s = counts / I[i].sum() if counts > 0 else 1.0
-        a = np.sqrt(s * I[i])
+        if counts < 0:
+            a = I[i].copy()
+        else:
+            s = counts / I[i].sum() if counts > 0 else 1.0
+            a = np.sqrt(s * I[i])
         if noise is not None:
             a = np.maximum(a + 0.5 * np.asarray(noise[i], np.float64), 0.0)
         out[i] = gain * np.fft.fftshift(np.log1p(a * a))

@@ -294,9 +294,10 @@ __global__ void __launch_bounds__(1024) k_sigmoid_mse(const float* __restrict__ 
 }
 
 // Network input from detector images [nimg][nz][ny] (natural FFT order):
-// s = counts / sum(I) (s = 1 when counts <= 0), amplitude a = sqrt(s I), plus
-// 0.5 * noise when given (the standard deviation of a Poisson amplitude), and
-// x = gain * log(1 + a^2), written centred (fftshift).  One block per image.
+// s = counts / sum(I) (s = 1 when counts == 0), amplitude a = sqrt(s I) (the
+// input itself when counts < 0), plus 0.5 * noise when given (the standard
+// deviation of a Poisson amplitude), and x = gain * log(1 + a^2), written
+// centred (fftshift).  One block per image.
 __global__ void __launch_bounds__(1024) k_detector_features(const float* __restrict__ I,
                                                             const float* __restrict__ noise, float* __restrict__ x,
                                                             int nz, int ny, float counts, float gain) {
@@ -324,7 +325,7 @@ __global__ void __launch_bounds__(1024) k_detector_features(const float* __restr
     for (size_t o = threadIdx.x; o < npx; o += blockDim.x) {
         const int zz = (int)(o / ny), yy = (int)(o % ny);
         const size_t src = (size_t)((zz + nz / 2) % nz) * ny + (size_t)((yy + ny / 2) % ny);
-        float a = sqrtf(sc * Ii[src]);
+        float a = counts < 0.f ? Ii[src] : sqrtf(sc * Ii[src]);
         if (noise) a = fmaxf(fmaf(0.5f, noise[blockIdx.x * npx + src], a), 0.f);
         x[blockIdx.x * npx + o] = gain * log1pf(a * a);
     }

@@ -229,7 +229,7 @@ class PillarSampler:
     with ``counts`` expected photons and Poisson-amplitude noise."""
 
     def __init__(self, params, coarse, base, n_pillars=(4, 16), foot=(2, 9), height=(1, 9), counts=1e6,
-                 chunk=16, gain=0.25):
+                 chunk=16, gain=0.25, tune=False):
         self.p1 = params
         self.c = coarse
         self.shape = (coarse.cx, coarse.cz, coarse.cy)
@@ -242,6 +242,9 @@ class PillarSampler:
                                 slice_nm=params.slice_nm, dy_nm=params.dy_nm, dz_nm=params.dz_nm,
                                 flags=B.MSLICE_PER_STRUCTURE)
         dev = base.device
+        if tune:
+            from . import autotune
+            autotune.apply(self.pb, dev)
         self.npx = ny * nz
         self.vols = base.reshape(1, ns, nz, ny).repeat(self.chunk, 1, 1, 1).contiguous()
         self.ws = B.workspace(self.pb, B.MSLICE_OP_FORWARD, dev)
@@ -286,8 +289,8 @@ class PillarSampler:
     def features_of(self, meas_amp):
         """Network input from a measured amplitude sqrt(counts) [nz][ny]."""
         x = torch.empty(self.npx, dtype=torch.float32, device=self.dev)
-        a2 = (meas_amp.reshape(-1) * meas_amp.reshape(-1)).contiguous()
-        B.mslice_nn_detector_features(a2, None, x, 1, self.p1.nz, self.p1.ny, 0.0, self.gain)
+        B.mslice_nn_detector_features(meas_amp.reshape(-1).contiguous(), None, x, 1, self.p1.nz, self.p1.ny, -1.0,
+                                      self.gain)
         return x.view(1, self.p1.nz, self.p1.ny)
 
 
@@ -302,7 +305,7 @@ def train(net, sampler, n_samples, batch, lr=1e-3, seed=1000, log_every=0):
         x, occ, _ = sampler.sample(rng, nb, gen=gen)
         rl = net.loss_grad(x, occ, nb)
         net.adam(lr)
-        losses.append(rl.sum())
+        losses.append(rl.clone())
         if log_every and (i // batch) % log_every == 0:
-            print("samples %d loss %.5f" % (i + nb, float(losses[-1])), flush=True)
-    return [float(v) for v in torch.stack(losses).cpu()]
+            print("samples %d loss %.5f" % (i + nb, float(losses[-1].cpu().numpy().sum())), flush=True)
+    return [float(v.sum()) for v in (t.cpu().numpy() for t in losses)]

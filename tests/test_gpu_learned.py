@@ -101,7 +101,7 @@ def test_detector_features_vs_oracle():
     I = (rng.random((3, 32, 64)) ** 4).astype(np.float32)
     noise = rng.standard_normal(I.shape).astype(np.float32)
     x = torch.empty(I.size, dtype=torch.float32, device="cuda")
-    for nz_, counts in ((noise, 1e6), (None, 1e5), (None, 0.0)):
+    for nz_, counts in ((noise, 1e6), (None, 1e5), (None, 0.0), (noise, -1.0)):
         B.mslice_nn_detector_features(G.dev(I, np.float32), None if nz_ is None else G.dev(nz_, np.float32), x,
                                       3, 32, 64, counts, 0.25)
         ref = onn.detector_features(I, nz_, counts, 0.25)
@@ -182,7 +182,7 @@ def test_trained_network_gains_over_zero_and_constant_starts():
     k = len(losses) // 10
     assert np.mean(losses[-k:]) < 0.9 * np.mean(losses[:k]), losses
     _, occ, _ = sampler.sample(np.random.default_rng(999), 256, noise=False)
-    occ_mean = float(occ.mean())
+    occ_mean = float(occ.cpu().numpy().mean())
     ws = B.workspace(p, B.MSLICE_OP_FORWARD)
     for seed in (100001, 100002, 100003):
         _, _, theta = sampler.sample(np.random.default_rng(seed), 1, noise=False)

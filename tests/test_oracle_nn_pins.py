@@ -131,8 +131,10 @@ def test_detector_features_scaling_and_centring():
     np.testing.assert_allclose(a2.sum(axis=(1, 2)), [1e4, 1e4], rtol=1e-12)
     # the DC pixel lands at the centre
     assert x[0, 4, 8] == pytest.approx(np.log1p(1e4 * I[0, 0, 0] / I[0].sum()), rel=1e-13)
-    # counts <= 0: input already in counts
+    # counts == 0: input already in counts; counts < 0: input is the amplitude
     np.testing.assert_allclose(nn.detector_features(I, counts=0, gain=2.0)[1, 4, 8], 2 * np.log1p(I[1, 0, 0]))
+    np.testing.assert_allclose(nn.detector_features(I, counts=-1, gain=2.0)[1, 4, 8],
+                               2 * np.log1p(I[1, 0, 0] ** 2))
 
 
 def test_rasterize_boxes_by_loops():

@@ -308,7 +308,9 @@ struct Grid {
         if (threadIdx.x == 0) {
             int ok = 1;
             const unsigned target = epoch * nblocks + withhold;
-            __threadfence();
+            // The block's writes are ordered before this thread by the
+            // __syncthreads above; the gpu-scope release publishes them and the
+            // acquire loads below order the other blocks' writes before ours.
             red_release_add(&ctrl[1], 1u);
             unsigned long long t0 = globaltimer();
             unsigned spins = 0;
@@ -323,7 +325,6 @@ struct Grid {
                     __nanosleep(32);
                 }
             }
-            __threadfence();
             *(volatile int*)s_ok = ok;
         }
         __syncthreads();
@@ -334,10 +335,7 @@ struct Grid {
     // when it needs the other blocks' results, doing other work in between.
     __device__ __forceinline__ void arrive(int slot) {
         __syncthreads();
-        if (threadIdx.x == 0) {
-            __threadfence();
-            red_release_add(&ctrl[slot], 1u);
-        }
+        if (threadIdx.x == 0) red_release_add(&ctrl[slot], 1u);
     }
     // Wait until every block made `arrivals` arrivals on ctrl[slot]; false
     // (uniformly per block) on timeout or an error reported by another block.
@@ -358,7 +356,6 @@ struct Grid {
                     __nanosleep(32);
                 }
             }
-            __threadfence();
             *(volatile int*)s_ok = ok;
         }
         __syncthreads();

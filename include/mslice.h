@@ -73,6 +73,11 @@ extern "C" {
                                     vol and grad_vol are [nw][ns][nz][ny] (nw
                                     independent structures of one grid shape,
                                     each with its own incidence angle) */
+#define MSLICE_EXACT_TRANSMISSION 4u  /* Eq. 1 with the exact 1 - n^2 = 2w - w^2,
+                                         w = delta - i beta: t = exp(-i k Delta
+                                         (w - w^2/2)) instead of the linearised
+                                         exp(-i k Delta w); the gradient follows
+                                         (d log t / dw = -i k Delta (1 - w)) */
 
 typedef struct mslice_params {
     double wavelength_nm;      /* lambda; k = 2 pi / lambda is formed in FP64 */
@@ -85,7 +90,7 @@ typedef struct mslice_params {
     double alpha_i_rad[MSLICE_MAX_ANGLES]; /* incidence angle of each wavefield */
     double psi_rad;            /* in-plane (yaw) angle: must be 0 */
     int32_t checkpoint_every;  /* adjoint segment length in slices; <= 0 means 32 */
-    uint32_t flags;            /* MSLICE_EXIT_WAVE, MSLICE_PER_STRUCTURE */
+    uint32_t flags;            /* MSLICE_EXIT_WAVE, MSLICE_PER_STRUCTURE, MSLICE_EXACT_TRANSMISSION */
     int32_t grid_blocks;       /* launch shape: blocks of the persistent kernels, 0 = automatic
                                   (capped at the co-resident maximum) */
     int32_t col_width;         /* launch shape: columns per column-pass group (4, 8 or 16),

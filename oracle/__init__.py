@@ -64,6 +64,7 @@ class OrcParams(ctypes.Structure):
         ("alpha_i_rad", ctypes.POINTER(ctypes.c_double)),
         ("force_naive_dft", ctypes.c_int32),
         ("exit_wave", ctypes.c_int32),
+        ("exact", ctypes.c_int32),
     ]
 
 
@@ -95,8 +96,10 @@ class Geometry:
     """Grid and beam: lambda, Delta, dy, dz, (Ny, Nz, Ns) and the incidence angles."""
 
     def __init__(self, ny, nz, ns, wavelength_nm=0.155, slice_nm=20.0, dy_nm=2.0,
-                 dz_nm=2.0, alpha_i_deg=(0.3,)):
+                 dz_nm=2.0, alpha_i_deg=(0.3,), exact_transmission=False):
         self.ny, self.nz, self.ns = int(ny), int(nz), int(ns)
+        # exact 1 - n^2 in the transmission of Eq. 1 instead of 2 (delta - i beta)
+        self.exact_transmission = bool(exact_transmission)
         self.wavelength_nm = float(wavelength_nm)
         self.slice_nm = float(slice_nm)
         self.dy_nm, self.dz_nm = float(dy_nm), float(dz_nm)
@@ -111,7 +114,7 @@ class Geometry:
         return OrcParams(self.wavelength_nm, self.slice_nm, self.dy_nm, self.dz_nm,
                          self.ny, self.nz, self.ns, self.nw,
                          self._alpha_keep.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
-                         int(bool(naive)), int(bool(exit_wave)))
+                         int(bool(naive)), int(bool(exit_wave)), int(self.exact_transmission))
 
 
 def _c128(a, shape):

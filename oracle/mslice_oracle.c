@@ -17,7 +17,8 @@
  *   for slice j = 1 .. Ns:                                   (Eq. 1)
  *       a_j   = exp(-i k Delta (delta_j - i beta_j)) * phi_{j-1}
  *               (transmission exp((k/2i) int (1-n^2) dZ) with n = 1-delta+i beta,
- *                linearised 1-n^2 ~ 2(delta - i beta), one voxel per slice)
+ *                linearised 1-n^2 ~ 2(delta - i beta), one voxel per slice;
+ *                with `exact`, 1-n^2 = 2w - w^2, w = delta - i beta)
  *       phi_j = F^-1 [ exp(-i Delta (k_y^2 + k_z^2) / 2k) * F a_j ]
  *               (paraxial Fresnel propagator "C" of Fig. 1; the global phase
  *                exp(i k Delta) is dropped: it never changes |Psi|^2)
@@ -69,6 +70,7 @@ typedef struct {
     const double *alpha_i_rad;/* [nw] incidence angles (probe tilted toward -z) */
     int32_t force_naive_dft;  /* 1: use the O(N^2) DFT at every size */
     int32_t exit_wave;        /* 1: forward returns phi_Ns (full last propagation) instead of Psi */
+    int32_t exact;            /* 1: exact 1 - n^2 in the transmission instead of 2 (delta - i beta) */
 } orc_params;
 
 static int is_pow2(int n) { return n >= 1 && (n & (n - 1)) == 0; }
@@ -197,8 +199,14 @@ static cplx *make_propagator(const orc_params *q)
     return P;
 }
 
-/* transmission of one voxel v = delta + i beta: exp(-i k Delta (delta - i beta)) */
-static cplx transmission(cplx v, double kd) { return cexp(-I * kd * conj(v)); }
+/* transmission of one voxel v = delta + i beta, w = delta - i beta:
+ * exp((k/2i) Delta (1 - n^2)) with n = 1 - w; 1 - n^2 = 2 w - w^2 (Eq. 1), so
+ * exp(-i k Delta (w - w^2/2)); linearised (exact == 0): exp(-i k Delta w) */
+static cplx transmission(cplx v, double kd, int exact)
+{
+    const cplx w = conj(v);
+    return cexp(-I * kd * (exact ? w - 0.5 * w * w : w));
+}
 
 static int check(const orc_params *q)
 {
@@ -247,7 +255,7 @@ static void forward_one(const orc_params *q, const plan2 *p, const cplx *P, cons
     for (int j = 0; j < q->ns; j++) {
         const cplx *v = vol + (size_t)j * npx;
 #pragma omp parallel for schedule(static)
-        for (size_t i = 0; i < npx; i++) phi[i] = transmission(v[i], kd) * phi[i];
+        for (size_t i = 0; i < npx; i++) phi[i] = transmission(v[i], kd, q->exact) * phi[i];
         if (a_store) memcpy(a_store + (size_t)j * npx, phi, sizeof(cplx) * npx);
         if (j < q->ns - 1) propagate(p, P, phi, 0);
     }
@@ -346,9 +354,11 @@ static void adjoint_one(const orc_params *q, const plan2 *p, const cplx *P, cons
 #pragma omp parallel for schedule(static)
         for (size_t i = 0; i < npx; i++) {
             cplx ag = a[i] * conj(g[i]);
-            /* dL/ddelta + i dL/dbeta = kd*Im(ag) - i kd*Re(ag) = -i kd ag */
-            gr[i] += -I * kd * ag;
-            g[i] = conj(transmission(v[i], kd)) * g[i];
+            /* dL/ddelta + i dL/dbeta = -i kd ag (d log t / dw = -i kd), times
+             * (1 - w) for the exact form (d log t / dw = -i kd (1 - w)) */
+            const cplx dw = q->exact ? 1.0 - conj(v[i]) : 1.0;
+            gr[i] += -I * kd * dw * ag;
+            g[i] = conj(transmission(v[i], kd, q->exact)) * g[i];
         }
         if (j > 0) propagate(p, P, g, 1);
     }

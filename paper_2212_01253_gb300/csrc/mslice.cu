@@ -85,11 +85,22 @@ __global__ void k_setup(const SetupArgs S) {
 // FP64 constant k Delta = kd_hi + kd_lo (two floats): fmaf(v, kd_hi, v * kd_lo)
 // is within one float ulp of the FP64 product, without FP64 arithmetic per
 // voxel.  Two voxels per thread and iteration (16-byte accesses).
+// exact 1 - n^2 (Eq. 1): t = exp(-i kd (w - w^2/2)), w = delta - i beta, i.e. the
+// linearised form evaluated at delta' = delta - (delta^2 - beta^2)/2 and
+// beta' = beta (1 - delta)
+__device__ __forceinline__ float2 exact_dbeta(float d, float b) {
+    return make_float2(d - 0.5f * (d * d - b * b), b * (1.f - d));
+}
+
 __global__ void k_transmission(const float4* __restrict__ vol, float4* __restrict__ tv, size_t n2, float kd_hi,
-                               float kd_lo) {
+                               float kd_lo, int exact) {
     const size_t stride = (size_t)gridDim.x * blockDim.x;
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += stride) {
-        const float4 v = __ldcs(vol + i);
+        float4 v = __ldcs(vol + i);
+        if (exact) {
+            const float2 e0 = exact_dbeta(v.x, v.y), e1 = exact_dbeta(v.z, v.w);
+            v = make_float4(e0.x, e0.y, e1.x, e1.y);
+        }
         float s0, c0, s1, c1;
         sincosf(fmaf(v.x, kd_hi, v.x * kd_lo), &s0, &c0);
         sincosf(fmaf(v.z, kd_hi, v.z * kd_lo), &s1, &c1);
@@ -101,8 +112,8 @@ __global__ void k_transmission(const float4* __restrict__ vol, float4* __restric
 
 // odd voxel count: the last voxel
 __global__ void k_transmission_tail(const float2* __restrict__ vol, float2* __restrict__ tv, float kd_hi,
-                                    float kd_lo) {
-    const float2 v = vol[0];
+                                    float kd_lo, int exact) {
+    const float2 v = exact ? exact_dbeta(vol[0].x, vol[0].y) : vol[0];
     float s, c;
     sincosf(fmaf(v.x, kd_hi, v.x * kd_lo), &s, &c);
     const float a = expf(-fmaf(v.y, kd_hi, v.y * kd_lo));
@@ -138,7 +149,7 @@ int validate(const mslice_params* p) {
     for (int w = 0; w < p->nw; ++w)
         if (!(fabs(p->alpha_i_rad[w]) < 1.5707963)) return MSLICE_EINVAL;
     if (p->psi_rad != 0.0) return MSLICE_EUNSUPPORTED;
-    if (p->flags & ~(MSLICE_EXIT_WAVE | MSLICE_PER_STRUCTURE)) return MSLICE_EINVAL;
+    if (p->flags & ~(MSLICE_EXIT_WAVE | MSLICE_PER_STRUCTURE | MSLICE_EXACT_TRANSMISSION)) return MSLICE_EINVAL;
     if (p->grid_blocks < 0 || p->col_width < 0 || p->schedule < 0 || p->schedule > 2) return MSLICE_EINVAL;
     if (p->col_width > 0 && !col_cw_ok(p->col_width, p->nz > 32 ? p->nz / 32 : 1)) return MSLICE_EINVAL;
     return MSLICE_OK;
@@ -338,18 +349,18 @@ int launch_coop(const void* fn, int grid, size_t smem, const SweepArgs& a, cudaS
     return note(e, "cudaLaunchCooperativeKernel") ? MSLICE_ELAUNCH : MSLICE_OK;
 }
 
-int launch_transmission(const float2* vol, float2* tv, size_t nvox, double kd, cudaStream_t st) {
+int launch_transmission(const float2* vol, float2* tv, size_t nvox, double kd, int exact, cudaStream_t st) {
     const float kd_hi = (float)kd;
     const float kd_lo = (float)(kd - (double)kd_hi);
     const size_t n2 = nvox / 2;
     if (n2) {
         size_t tb = (n2 + 255) / 256;
         if (tb > 152 * 16) tb = 152 * 16;
-        k_transmission<<<(unsigned)tb, 256, 0, st>>>((const float4*)vol, (float4*)tv, n2, kd_hi, kd_lo);
+        k_transmission<<<(unsigned)tb, 256, 0, st>>>((const float4*)vol, (float4*)tv, n2, kd_hi, kd_lo, exact);
         if (note(cudaGetLastError(), "k_transmission launch")) return MSLICE_ELAUNCH;
     }
     if (nvox & 1) {
-        k_transmission_tail<<<1, 1, 0, st>>>(vol + nvox - 1, tv + nvox - 1, kd_hi, kd_lo);
+        k_transmission_tail<<<1, 1, 0, st>>>(vol + nvox - 1, tv + nvox - 1, kd_hi, kd_lo, exact);
         if (note(cudaGetLastError(), "k_transmission_tail launch")) return MSLICE_ELAUNCH;
     }
     return MSLICE_OK;
@@ -400,7 +411,8 @@ int prepare(const mslice_params* p, int op, const float* vol, const float* probe
     const double kd = 2.0 * M_PI / p->wavelength_nm * p->slice_nm;
     const size_t nvox = (size_t)p->ns * p->ny * p->nz * ((p->flags & MSLICE_PER_STRUCTURE) ? p->nw : 1);
     r = prof_begin(KID_TRANSMISSION, (double)nvox, st);
-    rc = launch_transmission((const float2*)vol, (float2*)(w + L.tvol), nvox, kd, st);
+    const int exact = (p->flags & MSLICE_EXACT_TRANSMISSION) ? 1 : 0;
+    rc = launch_transmission((const float2*)vol, (float2*)(w + L.tvol), nvox, kd, exact, st);
     prof_end(r, st);
     if (rc) return rc;
     SweepArgs& a = P->base;
@@ -410,6 +422,8 @@ int prepare(const mslice_params* p, int op, const float* vol, const float* probe
     a.ffy = (float)(1.0 / sqrt((double)p->ny));
     a.ffz = (float)(1.0 / sqrt((double)p->nz));
     a.tvol = (const float2*)(w + L.tvol);
+    a.vol = (const float2*)vol;
+    a.exact = exact;
     a.probe = (const float2*)probe;
     a.probe_z = (const float2*)(w + L.probe_z);
     a.tab = (const float2*)(w + L.tab);
@@ -618,7 +632,9 @@ int mslice_transmission(const mslice_params* p, const float* vol, float* t_out, 
     if (!vol || !t_out || ((uintptr_t)vol & 15) || ((uintptr_t)t_out & 15)) return MSLICE_EINVAL;
     const double kd = 2.0 * M_PI / p->wavelength_nm * p->slice_nm;
     const size_t nvox = (size_t)p->ns * p->ny * p->nz;
-    return launch_transmission((const float2*)vol, (float2*)t_out, nvox, kd, (cudaStream_t)stream);
+    const size_t nv = nvox * ((p->flags & MSLICE_PER_STRUCTURE) ? p->nw : 1);
+    return launch_transmission((const float2*)vol, (float2*)t_out, nv, kd,
+                               (p->flags & MSLICE_EXACT_TRANSMISSION) ? 1 : 0, (cudaStream_t)stream);
 }
 
 int mslice_intensity_vjp(const float* psi, const float* dI, float* g_psi, size_t n, void* stream) {

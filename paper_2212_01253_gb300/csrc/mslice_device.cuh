@@ -390,6 +390,7 @@ struct SweepArgs {
     float ffy, ffz;     // 1/sqrt(ny), 1/sqrt(nz)
     float scale;        // loss s
     const float2* tvol;     // [ns][nz][ny] transmission
+    const float2* vol;      // [ns][nz][ny] delta + i beta (read by the adjoint when exact)
     const float2* probe;    // [nw][nz][ny] or null
     const float2* probe_z;  // [nw][nz] default probe rows
     const float2* tab;      // Wt_y[ny] | Wt_z[nz] | P_y[ny]/ny | P_z[nz]/nz
@@ -418,6 +419,7 @@ struct SweepArgs {
     int per_w;              // 1: wavefield w has its own volume (tvol, grad: [nw][ns][nz][ny])
     int lcw;                // log2 of the columns per column-pass group
     int split;              // 1: two wavefield groups with split-phase barriers
+    int exact;              // 1: exact 1 - n^2 transmission (gradient factor 1 - conj(v))
     float scales[MSLICE_MAX_ANGLES];  // per-wavefield loss scale when per_w
 };
 
@@ -533,19 +535,46 @@ __device__ void row_pass(const SweepArgs& A, const Smem& S, const int j, const b
                 const float2* a = A.seg + (size_t)(j - A.seg_base) * A.nw * npx + row;
                 float2* gdst = (A.nw == 1 || A.per_w) ? (A.grad + vol_offset(A, w, j, z, N))
                                                       : (A.gpart + (size_t)(A.split & j) * A.nw * npx + row);
+                if (!A.exact) {
 #pragma unroll
-                for (int c = 0; c < 32; c += MS_ADJ_CHUNK) {
-                    float2 av[MS_ADJ_CHUNK];
+                    for (int c = 0; c < 32; c += MS_ADJ_CHUNK) {
+                        float2 av[MS_ADJ_CHUNK];
 #pragma unroll
-                    for (int k = 0; k < MS_ADJ_CHUNK; ++k)
-                        if (c + k < P) av[k] = __ldcg(a + t + T * (c + k));
+                        for (int k = 0; k < MS_ADJ_CHUNK; ++k)
+                            if (c + k < P) av[k] = __ldcg(a + t + T * (c + k));
 #pragma unroll
-                    for (int k = 0; k < MS_ADJ_CHUNK; ++k) {
-                        if (c + k < P) {
-                            const float2 g = x[c + k];
-                            const float re = fmaf(av[k].x, g.x, av[k].y * g.y);   // Re(a conj g)
-                            const float im = fmaf(av[k].y, g.x, -av[k].x * g.y);  // Im(a conj g)
-                            __stcg(gdst + t + T * (c + k), make_float2(A.kd * im, -A.kd * re));
+                        for (int k = 0; k < MS_ADJ_CHUNK; ++k) {
+                            if (c + k < P) {
+                                const float2 g = x[c + k];
+                                const float re = fmaf(av[k].x, g.x, av[k].y * g.y);   // Re(a conj g)
+                                const float im = fmaf(av[k].y, g.x, -av[k].x * g.y);  // Im(a conj g)
+                                __stcg(gdst + t + T * (c + k), make_float2(A.kd * im, -A.kd * re));
+                            }
+                        }
+                    }
+                } else {
+                    // exact transmission: d log t / dw = -i kd (1 - w), w = conj(v)
+                    const float2* vv = A.vol + vol_offset(A, w, j, z, N);
+#pragma unroll
+                    for (int c = 0; c < 32; c += 8) {
+                        float2 av[8], vk[8];
+#pragma unroll
+                        for (int k = 0; k < 8; ++k) {
+                            if (c + k < P) {
+                                av[k] = __ldcg(a + t + T * (c + k));
+                                vk[k] = __ldg(vv + t + T * (c + k));
+                            }
+                        }
+#pragma unroll
+                        for (int k = 0; k < 8; ++k) {
+                            if (c + k < P) {
+                                const float2 g = x[c + k];
+                                const float re = fmaf(av[k].x, g.x, av[k].y * g.y);
+                                const float im = fmaf(av[k].y, g.x, -av[k].x * g.y);
+                                const float fr = 1.f - vk[k].x, fi = vk[k].y;       // 1 - conj(v)
+                                const float cr = fmaf(fr, re, -fi * im), ci = fmaf(fr, im, fi * re);
+                                __stcg(gdst + t + T * (c + k), make_float2(A.kd * ci, -A.kd * cr));
+                            }
                         }
                     }
                 }

@@ -61,6 +61,39 @@ def test_transmission_fp64():
     assert np.abs(t.cpu().numpy() - ref).max() < 1e-6
 
 
+def test_exact_transmission_fp64():
+    """MSLICE_EXACT_TRANSMISSION: exp((k/2i) Delta (1 - n^2)), n = 1 - delta + i beta,
+    evaluated in FP64 from n."""
+    from paper_2212_01253_gb300 import binding as B
+    geo = oracle.Geometry(32, 64, 8, exact_transmission=True)
+    vol = ci.random_volume(4, 32, 64, 8, scale=100)
+    p = G.params(geo)
+    t = torch.empty(vol.shape, dtype=torch.complex64, device="cuda")
+    B.mslice_transmission(p, G.dev(vol, np.complex64), t)
+    k = 2 * np.pi / geo.wavelength_nm
+    n = 1 - vol.astype(np.complex64).astype(np.complex128).conj()
+    ref = np.exp(k / 2j * geo.slice_nm * (1 - n * n))
+    assert np.abs(t.cpu().numpy() - ref).max() < 1e-6
+    lin = np.exp(-1j * k * geo.slice_nm * np.conj(vol.astype(np.complex128)))
+    assert np.abs(ref - lin).max() > 1e-5       # the flag changes the result
+
+
+@pytest.mark.parametrize("ny,nz,ns,nw,K", [(64, 64, 24, 1, 5), (32, 64, 13, 3, 4), (512, 256, 20, 2, 20)])
+def test_exact_transmission_loss_grad_vs_oracle(ny, nz, ns, nw, K):
+    geo = oracle.Geometry(ny, nz, ns, alpha_i_deg=np.linspace(0.15, 0.45, nw), exact_transmission=True)
+    vol = ci.random_volume(ny + ns, ny, nz, ns, scale=60)
+    meas = _target(geo, vol.astype(np.complex128) * 1.1, 4)
+    L_ref, g_ref, I_ref = oracle.loss_grad(geo, vol, meas, 0.7, return_intensity=True)
+    L, g, I = G.loss_grad(geo, vol, meas, 0.7, checkpoint_every=K, return_intensity=True)
+    assert G.rel(I, I_ref) <= TOL_I
+    assert abs(L - L_ref) <= 1e-4 * abs(L_ref)
+    assert G.rel(g, g_ref) <= TOL_GRAD
+    # and it is not the linearised gradient
+    lin = oracle.Geometry(ny, nz, ns, alpha_i_deg=np.linspace(0.15, 0.45, nw))
+    _, g_lin = oracle.loss_grad(lin, vol, meas, 0.7)
+    assert G.rel(g_lin, g_ref) > 10 * G.rel(g, g_ref)
+
+
 # --------------------------------------------------------------------------
 # forward parity
 # --------------------------------------------------------------------------

@@ -265,10 +265,30 @@ def test_loss_matches_forward(oracle_lib):
     assert rel(I, oracle_lib.forward(geo, vol)) < 1e-14
 
 
-def test_gradient_central_differences(oracle_lib):
+def test_exact_transmission_from_refractive_index(oracle_lib):
+    """Eq. 1's transmission exp((k/2i) Delta (1 - n^2)) with n = 1 - delta + i beta,
+    evaluated directly from n, against the oracle's exact form; the linearised
+    form against exp(-i k Delta (delta - i beta)).  One uniform slice and an
+    untilted plane wave: the exit wave is the transmission itself."""
+    ny, nz = 8, 8
+    delta, beta = 3e-3, 4e-4            # large enough that 1 - n^2 differs visibly from 2(delta - i beta)
+    vol = np.full((1, nz, ny), delta + 1j * beta)
+    k = 2 * np.pi / 0.155
+    n = 1 - delta + 1j * beta
+    for exact, ref in ((True, np.exp(k / 2j * 20.0 * (1 - n * n))),
+                       (False, np.exp(-1j * k * 20.0 * (delta - 1j * beta)))):
+        geo = oracle_lib.Geometry(ny, nz, 1, alpha_i_deg=(0.0,), exact_transmission=exact)
+        phi = oracle_lib.forward(geo, vol, exit_wave=True)
+        assert np.abs(phi - ref).max() < 1e-12
+    # the two forms differ by k Delta |w|^2 / 2 in phase (about 3.7e-3 rad here)
+    assert abs(np.angle(np.exp(k / 2j * 20.0 * (1 - n * n)) / np.exp(-1j * k * 20.0 * (delta - 1j * beta)))) > 1e-3
+
+
+@pytest.mark.parametrize("exact", [False, True])
+def test_gradient_central_differences(oracle_lib, exact):
     """dL/ddelta and dL/dbeta on a 16x16x8 sub-volume of a 32x32x16 grid."""
     ny, nz, ns = 32, 32, 16
-    geo = oracle_lib.Geometry(ny, nz, ns, alpha_i_deg=(0.3,))
+    geo = oracle_lib.Geometry(ny, nz, ns, alpha_i_deg=(0.3,), exact_transmission=exact)
     vol = ci.random_volume(11, ny, nz, ns, scale=40).astype(np.complex128)
     probe = ci.random_probe(11, 1, ny, nz).astype(np.complex128)
     I0 = oracle_lib.forward(geo, vol, probe=probe)

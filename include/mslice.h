@@ -210,10 +210,15 @@ typedef struct mslice_coarse {
     int32_t cx, cz, cy;      /* coarse grid */
     int32_t bx, bz, by;      /* block size in fine voxels */
     int32_t x0, z0, y0;      /* fine-grid offset of the block */
-    float beta_ratio;        /* beta / delta of the material */
+    float beta_ratio;        /* d beta / d theta: the material's beta / delta (or the
+                                ratio of the differences for two materials) */
+    float base_delta;        /* delta + i beta of the block at theta = 0: 0 for voxels */
+    float base_beta;         /*   that are vacuum or material, the host material's index for
+                                inclusions buried in it (Sec. 4.1, Au in Si) */
 } mslice_coarse;
 
-/* vol[x0 + bx*a + i][z0 + bz*b + k][y0 + by*c + l] = theta[a][b][c] * (1 + i beta_ratio).
+/* vol[x0 + bx*a + i][z0 + bz*b + k][y0 + by*c + l]
+ *     = (base_delta + theta[a][b][c]) + i (base_beta + beta_ratio theta[a][b][c]).
  * theta float [cx][cz][cy]; vol complex [ns][nz][ny] (p gives ns, nz, ny). */
 int mslice_coarse_to_fine(const mslice_params *p, const mslice_coarse *c, const float *theta,
                           float *vol, void *stream);
@@ -223,6 +228,12 @@ int mslice_coarse_to_fine(const mslice_params *p, const mslice_coarse *c, const 
  * Each coarse voxel is summed by one thread in a fixed order (deterministic). */
 int mslice_fine_to_coarse(const mslice_params *p, const mslice_coarse *c, const float *grad_vol,
                           float *g_theta, void *stream);
+
+/* Material snapping of the coarse parameters (Sec. 4.1: after every 20 epochs
+ * each voxel is replaced by the nearest of the refractive indexes of interest):
+ * theta[i] = the level nearest to theta[i] (the lower one on a tie), for
+ * 1 <= nlevels <= 8 levels given in host memory; n parameters, in place. */
+int mslice_snap(float *theta, size_t n, const float *levels, int nlevels, void *stream);
 
 /* One ADAM step (Kingma & Ba, cited in Sec. 4.1) on n parameters, in place:
  *   m = b1 m + (1-b1) g;  v = b2 v + (1-b2) g^2;

@@ -212,9 +212,12 @@ def dft2d(x, sign=-1, naive=False):
 # multislice grid, and the ADAM update the paper optimises them with.
 # Plain numpy in double precision; definitions written out.
 # ---------------------------------------------------------------------------
-def coarse_to_fine(theta, fine_shape, block, offset=(0, 0, 0), beta_ratio=4.9e-6 / 4.7e-5, base=None):
+def coarse_to_fine(theta, fine_shape, block, offset=(0, 0, 0), beta_ratio=4.9e-6 / 4.7e-5, base=None,
+                   block_index=0j):
     """E: theta[cx][cz][cy] -> volume [ns][nz][ny]; every fine voxel of a coarse
-    block gets delta = theta and beta = beta_ratio * theta; others keep ``base``."""
+    block gets delta = Re(block_index) + theta and beta = Im(block_index) +
+    beta_ratio * theta (block_index: the index at theta = 0, e.g. the host
+    material of buried inclusions); voxels outside the blocks keep ``base``."""
     theta = np.asarray(theta, dtype=np.float64)
     vol = np.zeros(fine_shape, np.complex128) if base is None else np.array(base, np.complex128)
     cx, cz, cy = theta.shape
@@ -225,7 +228,7 @@ def coarse_to_fine(theta, fine_shape, block, offset=(0, 0, 0), beta_ratio=4.9e-6
             for c in range(cy):
                 d = theta[a, b, c]
                 vol[x0 + a * bx:x0 + (a + 1) * bx, z0 + b * bz:z0 + (b + 1) * bz,
-                    y0 + c * by:y0 + (c + 1) * by] = d + 1j * beta_ratio * d
+                    y0 + c * by:y0 + (c + 1) * by] = complex(block_index) + d + 1j * beta_ratio * d
     return vol
 
 
@@ -243,6 +246,15 @@ def fine_to_coarse(grad, coarse_shape, block, offset=(0, 0, 0), beta_ratio=4.9e-
                            y0 + c * by:y0 + (c + 1) * by]
                 g[a, b, c] = (blk.real + beta_ratio * blk.imag).sum()
     return g
+
+
+def snap(theta, levels):
+    """Material snapping (Sec. 4.1): each parameter becomes the nearest level,
+    the lower one when two are equally near."""
+    theta = np.asarray(theta, dtype=np.float64)
+    lv = np.sort(np.asarray(levels, dtype=np.float64))
+    d = np.abs(theta[..., None] - lv)            # argmin takes the first (lowest) level on a tie
+    return lv[np.argmin(d, axis=-1)]
 
 
 def adam_step(theta, m, v, grad, lr, b1, b2, eps, t, lo=-np.inf, hi=np.inf):

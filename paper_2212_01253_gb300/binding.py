@@ -81,16 +81,18 @@ class mslice_coarse(ctypes.Structure):
     _fields_ = [("cx", ctypes.c_int32), ("cz", ctypes.c_int32), ("cy", ctypes.c_int32),
                 ("bx", ctypes.c_int32), ("bz", ctypes.c_int32), ("by", ctypes.c_int32),
                 ("x0", ctypes.c_int32), ("z0", ctypes.c_int32), ("y0", ctypes.c_int32),
-                ("beta_ratio", ctypes.c_float)]
+                ("beta_ratio", ctypes.c_float), ("base_delta", ctypes.c_float), ("base_beta", ctypes.c_float)]
 
 
-def make_coarse(shape, block, offset=(0, 0, 0), beta_ratio=4.9e-6 / 4.7e-5):
-    """mslice_coarse for a coarse grid shape (cx, cz, cy), block (bx, bz, by) and fine offset."""
+def make_coarse(shape, block, offset=(0, 0, 0), beta_ratio=4.9e-6 / 4.7e-5, base=0j):
+    """mslice_coarse for a coarse grid shape (cx, cz, cy), block (bx, bz, by), fine
+    offset, d beta / d theta and the block's index at theta = 0 (``base``, complex)."""
     c = mslice_coarse()
     c.cx, c.cz, c.cy = (int(v) for v in shape)
     c.bx, c.bz, c.by = (int(v) for v in block)
     c.x0, c.z0, c.y0 = (int(v) for v in offset)
     c.beta_ratio = float(beta_ratio)
+    c.base_delta, c.base_beta = float(complex(base).real), float(complex(base).imag)
     return c
 
 
@@ -132,6 +134,7 @@ def _load():
                 "mslice_profile_enable": ([ctypes.c_int], ctypes.c_int),
                 "mslice_coarse_to_fine": ([P, ctypes.POINTER(mslice_coarse), vp, vp, vp], ctypes.c_int),
                 "mslice_fine_to_coarse": ([P, ctypes.POINTER(mslice_coarse), vp, vp, vp], ctypes.c_int),
+                "mslice_snap": ([vp, sz, ctypes.POINTER(ctypes.c_float), ctypes.c_int, vp], ctypes.c_int),
                 "mslice_adam_step": ([vp, vp, vp, vp, sz, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                                       ctypes.c_float, ctypes.c_int, ctypes.c_float, ctypes.c_float, vp],
                                      ctypes.c_int),
@@ -413,3 +416,10 @@ def mslice_nn_rasterize_boxes(boxes, out, shape, value, stream=None):
     _check(_load().mslice_nn_rasterize_boxes(
         _ptr(boxes, torch.int32, ns_ * nb_ * 6, "boxes"), nb_, ns_, d0, d1, d2, float(value),
         _ptr(out, torch.float32, ns_ * d0 * d1 * d2, "out"), _stream(stream)), "mslice_nn_rasterize_boxes")
+
+
+def mslice_snap(theta, levels, stream=None):
+    """In place: every parameter becomes the nearest of ``levels`` (1..8 floats)."""
+    lv = (ctypes.c_float * len(levels))(*[float(v) for v in levels])
+    _check(_load().mslice_snap(_ptr(theta, torch.float32, None, "theta"), theta.numel(), lv, len(levels),
+                               _stream(stream)), "mslice_snap")

@@ -30,7 +30,7 @@ __global__ void k_coarse_to_fine(const float* __restrict__ theta, float2* __rest
         float2* out = vol + ((size_t)(c.x0 + xx) * nz + (c.z0 + zz)) * ny + c.y0;
         for (int yy = threadIdx.x; yy < bys; yy += blockDim.x) {
             const float d = __ldg(th + yy / c.by);
-            out[yy] = make_float2(d, c.beta_ratio * d);
+            out[yy] = make_float2(c.base_delta + d, fmaf(c.beta_ratio, d, c.base_beta));
         }
     }
 }
@@ -71,6 +71,28 @@ __global__ void k_adam(float* __restrict__ th, float* __restrict__ m, float* __r
     }
 }
 
+struct SnapLevels {
+    float v[8];
+    int n;
+};
+
+// nearest level, the lower one on a tie (levels in any order)
+__global__ void k_snap(float* __restrict__ th, size_t n, SnapLevels L) {
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const float x = th[i];
+        float best = L.v[0], bd = fabsf(x - L.v[0]);
+        for (int k = 1; k < L.n; ++k) {
+            const float d = fabsf(x - L.v[k]);
+            if (d < bd || (d == bd && L.v[k] < best)) {
+                bd = d;
+                best = L.v[k];
+            }
+        }
+        th[i] = best;
+    }
+}
+
 unsigned blocks_for(size_t n) {
     size_t b = (n + 255) / 256;
     return (unsigned)(b > 4096 ? 4096 : (b ? b : 1));
@@ -95,6 +117,16 @@ int mslice_fine_to_coarse(const mslice_params* p, const mslice_coarse* c, const 
     const size_t n = (size_t)c->cx * c->cz * c->cy;
     k_fine_to_coarse<<<blocks_for(n), 256, 0, (cudaStream_t)stream>>>((const float2*)grad_vol, g_theta, *c, p->ny,
                                                                       p->nz);
+    return cudaGetLastError() == cudaSuccess ? MSLICE_OK : MSLICE_ELAUNCH;
+}
+
+int mslice_snap(float* theta, size_t n, const float* levels, int nlevels, void* stream) {
+    if (!theta || !levels || nlevels < 1 || nlevels > 8) return MSLICE_EINVAL;
+    if (n == 0) return MSLICE_OK;
+    SnapLevels L{};
+    for (int k = 0; k < nlevels; ++k) L.v[k] = levels[k];
+    L.n = nlevels;
+    k_snap<<<blocks_for(n), 256, 0, (cudaStream_t)stream>>>(theta, n, L);
     return cudaGetLastError() == cudaSuccess ? MSLICE_OK : MSLICE_ELAUNCH;
 }
 

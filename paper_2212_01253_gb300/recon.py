@@ -3,6 +3,7 @@
 loss of Eq. 4, ADAM).  Every step runs in libmslice kernels:
 
     E (coarse -> fine) -> mslice_loss_grad -> E^T -> ADAM (clamped to [lo, hi])
+    [-> material snapping every snap_every iterations]
 
 The fine volume keeps its fixed part (substrate, vacuum) outside the coarse
 block.  The stopping rule is the reduced chi^2 of Poisson amplitudes,
@@ -19,7 +20,7 @@ from . import binding as B
 
 class Reconstructor:
     def __init__(self, params, coarse, base_vol, meas_amp, scale, theta0=None, lr=2e-6, lo=0.0, hi=4.7e-5,
-                 b1=0.9, b2=0.999, eps=1e-20, probe=None):
+                 b1=0.9, b2=0.999, eps=1e-20, probe=None, snap_every=0, snap_levels=None, snap_start=0):
         dev = base_vol.device
         self.p, self.c = params, coarse
         self.vol = base_vol.clone()
@@ -38,6 +39,11 @@ class Reconstructor:
         self.lr, self.lo, self.hi, self.b1, self.b2, self.eps = lr, lo, hi, b1, b2, eps
         self.t = 0
         self.npix = params.nw * params.ny * params.nz
+        # material snapping (Sec. 4.1): every snap_every iterations (from
+        # iteration snap_start on) each coarse voxel becomes the nearest of snap_levels
+        self.snap_every = int(snap_every)
+        self.snap_levels = list(snap_levels) if snap_levels is not None else None
+        self.snap_start = int(snap_start)
 
     def step(self):
         """One iteration; returns nothing (the loss of the current theta lands in self.loss)."""
@@ -48,6 +54,8 @@ class Reconstructor:
         B.mslice_fine_to_coarse(self.p, self.c, self.grad, self.g_theta)
         B.mslice_adam_step(self.theta, self.m, self.v, self.g_theta, self.lr, self.b1, self.b2, self.eps,
                            self.t, self.lo, self.hi)
+        if self.snap_every and self.snap_levels and self.t >= self.snap_start and self.t % self.snap_every == 0:
+            B.mslice_snap(self.theta, self.snap_levels)
 
     def chi2(self):
         return 4.0 * float(self.loss.item()) / self.npix

@@ -83,3 +83,27 @@ def test_small_reconstruction_reduces_chi2():
     assert c2[-1] <= min(c2[:3]), c2
     assert c2[-1] < 0.6 * chi2_0, (chi2_0, chi2_gt, hist[-5:])
     assert c2[-1] > chi2_gt * 0.5
+
+
+def test_coarse_map_with_host_material_and_snapping_vs_oracle():
+    """E with a host material (Au inclusions buried in Si) and the snapping kernel
+    against the oracle: E bit for bit up to FP32 rounding of the index, snapping
+    exactly."""
+    from paper_2212_01253_gb300 import binding as B
+    ny, nz, ns = 64, 64, 40
+    shape, block, off = (6, 6, 6), (6, 4, 8), (2, 4, 8)
+    d_au = ci.AU.real - ci.SI.real
+    ratio = (ci.AU.imag - ci.SI.imag) / d_au
+    p = B.make_params(ny, nz, ns)
+    c = B.make_coarse(shape, block, off, beta_ratio=ratio, base=ci.SI)
+    rng = np.random.default_rng(8)
+    theta = rng.uniform(-0.2 * d_au, 1.2 * d_au, shape).astype(np.float32)
+    base = ci.substrate(ny, nz, ns)
+    vol = G.dev(base, np.complex64)
+    B.mslice_coarse_to_fine(p, c, G.dev(theta, np.float32), vol)
+    ref = oracle.coarse_to_fine(theta, (ns, nz, ny), block, off, beta_ratio=ratio, base=base,
+                                block_index=ci.SI)
+    assert np.abs(vol.cpu().numpy() - ref).max() <= 1e-7 * np.abs(ref).max()
+    th = G.dev(theta, np.float32)
+    B.mslice_snap(th, [0.0, float(np.float32(d_au))])
+    np.testing.assert_array_equal(th.cpu().numpy(), oracle.snap(theta, [0.0, float(np.float32(d_au))]))

@@ -377,3 +377,18 @@ def test_adam_first_step_and_convergence(oracle_lib):
     th, _, _ = oracle_lib.adam_step(np.zeros(1), np.zeros(1), np.zeros(1), np.array([-1.0]), 1.0, 0.9, 0.999,
                                     1e-8, 1, lo=0.0, hi=0.5)
     assert th[0] == 0.5
+
+
+def test_coarse_map_block_index_and_snapping(oracle_lib):
+    """E with a host material: theta = 0 gives exactly the host index, the map is
+    affine in theta with slope 1 + i beta_ratio; snapping picks the nearest level
+    and the lower one on a tie."""
+    th = np.array([[[0.0, 2.0]], [[1.0, -1.0]]])               # (cx, cz, cy) = (2, 1, 2)
+    host = 7.6e-6 + 1.75e-7j
+    vol = oracle_lib.coarse_to_fine(th, (4, 3, 4), (2, 1, 2), (0, 1, 0), beta_ratio=0.5, block_index=host)
+    assert vol[0, 1, 0] == host and vol[1, 1, 1] == host          # theta = 0
+    assert vol[0, 1, 2] == host + 2.0 + 1.0j                       # theta = 2
+    assert vol[3, 1, 3] == host - 1.0 - 0.5j                       # theta = -1
+    assert vol[0, 0, 0] == 0 and vol[0, 2, 0] == 0                 # outside the block
+    got = oracle_lib.snap([0.2, 0.5, 0.51, -3.0, 7.0, 4.0], [0.0, 1.0, 4.0])
+    np.testing.assert_array_equal(got, [0.0, 0.0, 1.0, 0.0, 4.0, 4.0])

@@ -55,33 +55,66 @@ __device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2
 __device__ __forceinline__ float2 cmul(float2 a, float2 w) {
     return make_float2(fmaf(a.x, w.x, -a.y * w.y), fmaf(a.x, w.y, a.y * w.x));
 }
+// a * (1 + u) and a * conj(1 + u), u = t - 1 from the transmission volume
+// (t is kept as t - 1: FP32 holds |u| ~ 1e-2 to ~1e-10 absolute, where it
+// holds t = 1 + u only to ~3e-8, an error that would repeat in every slice of
+// a uniform material)
+__device__ __forceinline__ float2 cmul_t(float2 a, float2 u) {
+    return make_float2(fmaf(a.x, u.x, fmaf(-a.y, u.y, a.x)), fmaf(a.x, u.y, fmaf(a.y, u.x, a.y)));
+}
+__device__ __forceinline__ float2 cmulc_t(float2 a, float2 u) {
+    return make_float2(fmaf(a.x, u.x, fmaf(a.y, u.y, a.x)), fmaf(a.y, u.x, fmaf(-a.x, u.y, a.y)));
+}
 // a * conj(w)
 __device__ __forceinline__ float2 cmulc(float2 a, float2 w) {
     return make_float2(fmaf(a.x, w.x, a.y * w.y), fmaf(a.y, w.x, -a.x * w.y));
 }
 
-// cos(pi e / 16) for e = 0..16, correctly rounded from the double values.  A
-// flat switch (no recursion) that is inlined and folds to an immediate when e
-// is a compile-time constant after unrolling.
-__host__ __device__ __forceinline__ constexpr float kcos32(int e) {
+// FP32 (cos, sin)(pi e / 16), e = 0..15, for the in-register radix stages,
+// written by csrc/gen_unit_twiddles.py: within six ulps of the correctly
+// rounded values, chosen so that c^2 + s^2 - 1 summed over the twiddles a
+// whole length-64..1024 transform applies is about zero (|drift| <= 5.7e-9).
+// Correctly rounded pairs all have c^2 + s^2 < 1, which makes every forward +
+// inverse transform lose ~5e-8 of the energy, identically in every slice
+// (1.4e-4 of the intensity after 1024 slices at 512^2).
+__host__ __device__ __forceinline__ constexpr float kTwC(int e) {
     switch (e) {
-        case 0: return 1.0f;
-        case 1: return (float)0.9807852804032304;
-        case 2: return (float)0.9238795325112867;
-        case 3: return (float)0.8314696123025452;
-        case 4: return (float)0.7071067811865476;
-        case 5: return (float)0.5555702330196023;
-        case 6: return (float)0.38268343236508984;
-        case 7: return (float)0.19509032201612833;
+        case 0: return 0x1.0000000000000p+0f;
+        case 1: return 0x1.f6297c0000000p-1f;
+        case 2: return 0x1.d906c00000000p-1f;
+        case 3: return 0x1.a9b6640000000p-1f;
+        case 4: return 0x1.6a09e60000000p-1f;
+        case 5: return 0x1.1c73b20000000p-1f;
+        case 6: return 0x1.87de200000000p-2f;
+        case 7: return 0x1.8f8b900000000p-3f;
         case 8: return 0.0f;
-        case 9: return -(float)0.19509032201612833;
-        case 10: return -(float)0.38268343236508984;
-        case 11: return -(float)0.5555702330196023;
-        case 12: return -(float)0.7071067811865476;
-        case 13: return -(float)0.8314696123025452;
-        case 14: return -(float)0.9238795325112867;
-        case 15: return -(float)0.9807852804032304;
-        default: return -1.0f;  // e = 16
+        case 9: return -0x1.8f8b900000000p-3f;
+        case 10: return -0x1.87de200000000p-2f;
+        case 11: return -0x1.1c73b20000000p-1f;
+        case 12: return -0x1.6a09e60000000p-1f;
+        case 13: return -0x1.a9b6640000000p-1f;
+        case 14: return -0x1.d906c00000000p-1f;
+        default: return -0x1.f6297c0000000p-1f;
+    }
+}
+__host__ __device__ __forceinline__ constexpr float kTwS(int e) {
+    switch (e) {
+        case 0: return 0.0f;
+        case 1: return 0x1.8f8b900000000p-3f;
+        case 2: return 0x1.87de200000000p-2f;
+        case 3: return 0x1.1c73b20000000p-1f;
+        case 4: return 0x1.6a09e60000000p-1f;
+        case 5: return 0x1.a9b6640000000p-1f;
+        case 6: return 0x1.d906c00000000p-1f;
+        case 7: return 0x1.f6297c0000000p-1f;
+        case 8: return 0x1.0000000000000p+0f;
+        case 9: return 0x1.f6297c0000000p-1f;
+        case 10: return 0x1.d906c00000000p-1f;
+        case 11: return 0x1.a9b6640000000p-1f;
+        case 12: return 0x1.6a09e60000000p-1f;
+        case 13: return 0x1.1c73b20000000p-1f;
+        case 14: return 0x1.87de200000000p-2f;
+        default: return 0x1.8f8b900000000p-3f;
     }
 }
 
@@ -106,8 +139,7 @@ template <bool INV>
 __device__ __forceinline__ float2 tw32(float2 a, int e) {
     if (e == 0) return a;
     if (e == 8) return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
-    const float c = kcos32(e);
-    const float s = kcos32(e <= 8 ? 8 - e : e - 8);  // sin(pi e / 16)
+    const float c = kTwC(e), s = kTwS(e);
     return INV ? make_float2(fmaf(a.x, c, -a.y * s), fmaf(a.y, c, a.x * s))
                : make_float2(fmaf(a.x, c, a.y * s), fmaf(a.y, c, -a.x * s));
 }
@@ -506,7 +538,7 @@ __device__ void row_pass(const SweepArgs& A, const Smem& S, const int j, const b
                 }
                 const float2* tv = A.tvol + vol_offset(A, w, j, z, N);
 #pragma unroll
-                for (int m = 0; m < 32; ++m) if (m < P) x[m] = cmul(x[m], __ldg(tv + t + T * m));
+                for (int m = 0; m < 32; ++m) if (m < P) x[m] = cmul_t(x[m], __ldg(tv + t + T * m));
                 if (j >= A.seg_from) {
                     float2* dst = A.seg + (size_t)(j - A.seg_base) * A.nw * npx + row;
 #pragma unroll
@@ -581,7 +613,7 @@ __device__ void row_pass(const SweepArgs& A, const Smem& S, const int j, const b
                 if (prop) {
                     const float2* tv = A.tvol + vol_offset(A, w, j, z, N);
 #pragma unroll
-                    for (int m = 0; m < 32; ++m) if (m < P) x[m] = cmulc(x[m], __ldg(tv + t + T * m));
+                    for (int m = 0; m < 32; ++m) if (m < P) x[m] = cmulc_t(x[m], __ldg(tv + t + T * m));
                 }
             }
             if (!prop) continue;  // uniform

@@ -93,22 +93,20 @@ __device__ __forceinline__ float2 exact_dbeta(float d, float b) {
 }
 
 // t of one voxel (minus_one = 0), or u = t - 1 (minus_one = 1) computed without
-// cancellation: Re u = (A - 1) + A (cos phi - 1) with A - 1 = expm1(-b) and
-// cos phi - 1 = -sin^2 phi / (1 + cos phi); Im u = -A sin phi.  The slice loops
-// apply t as a + a u: for the weak scatterers here |u| ~ 1e-2, so FP32 holds u
-// to ~1e-10 absolute where it holds t only to ~3e-8, an error that would
-// otherwise repeat in every slice of a uniform material.
+// cancellation.  With phi = kd delta, b = kd beta, A = exp(-b) and
+// (sh, ch) = (sin, cos)(phi / 2): sin phi = 2 sh ch, cos phi - 1 = -2 sh^2, so
+// Re u = (A - 1) - 2 A sh^2 with A - 1 = expm1(-b), Im u = -2 A sh ch.  The
+// slice loops apply t as a + a u: for the weak scatterers here |u| ~ 1e-2, so
+// FP32 holds u to ~1e-10 absolute where it holds t only to ~3e-8, an error
+// that would otherwise repeat in every slice of a uniform material.
 __device__ __forceinline__ float2 trans_value(float d, float b, float kd_hi, float kd_lo, int minus_one) {
-    float s, c;
-    sincosf(fmaf(d, kd_hi, d * kd_lo), &s, &c);
+    float sh, ch;
+    sincosf(fmaf(d, 0.5f * kd_hi, d * (0.5f * kd_lo)), &sh, &ch);   // phi / 2 (exact halving)
     const float at = fmaf(b, kd_hi, b * kd_lo);
-    if (!minus_one) {
-        const float a = expf(-at);
-        return make_float2(a * c, -a * s);
-    }
     const float em1 = expm1f(-at), a = 1.f + em1;
-    const float cm1 = c > 0.f ? -(s * s) / (1.f + c) : c - 1.f;
-    return make_float2(fmaf(a, cm1, em1), -a * s);
+    const float two_sh = 2.f * sh;
+    if (!minus_one) return make_float2(a * fmaf(-two_sh, sh, 1.f), -a * two_sh * ch);
+    return make_float2(fmaf(-a * two_sh, sh, em1), -a * two_sh * ch);
 }
 
 __global__ void k_transmission(const float4* __restrict__ vol, float4* __restrict__ tv, size_t n2, float kd_hi,

@@ -14,9 +14,10 @@
  *     free propagation to the detector are pure Fourier phases and are skipped).
  *   Eq. 4 (Sec. 4.1): the loss is the squared error of amplitudes; this library
  *     sums it (no 1/N): L = sum (sqrt(s I) - m)^2, m = sqrt(I_meas).
- *   Sec. 2, Eq. 2-3: the incidence angle alpha_i is applied by tilting the probe
- *     toward the substrate, phi_0(y, z) = exp(-i k sin(alpha_i) z), instead of
- *     rotating the volume (paraxially equivalent); psi (yaw) must be 0.
+ *   Sec. 2, Eq. 2-3: the incidence angle alpha_i and the in-plane angle psi are
+ *     applied by tilting the probe, phi_0(y, z) = exp(-i k (sin(alpha_i) z +
+ *     sin(psi) y)) (toward the substrate for alpha_i > 0), instead of rotating
+ *     the volume (paraxially equivalent).
  *
  * Axes and layouts (all arrays row-major, last index fastest):
  *   x  = slice index along the beam, ns slices of thickness slice_nm (Delta);
@@ -55,7 +56,7 @@ extern "C" {
 /* return codes */
 #define MSLICE_OK 0
 #define MSLICE_EINVAL (-1)        /* bad size, pointer, alignment or parameter */
-#define MSLICE_EUNSUPPORTED (-2)  /* valid request outside what is built (psi != 0, ...) */
+#define MSLICE_EUNSUPPORTED (-2)  /* valid request outside what is built */
 #define MSLICE_ELAUNCH (-3)       /* a CUDA launch or runtime call failed */
 #define MSLICE_ETIMEDOUT (-4)     /* a bounded device-side wait ran out */
 #define MSLICE_EWORKSPACE (-5)    /* workspace smaller than mslice_workspace_size() */
@@ -88,7 +89,9 @@ typedef struct mslice_params {
     int32_t ns;                /* number of slices, >= 1 */
     int32_t nw;                /* number of wavefields (incidence angles), 1..MSLICE_MAX_ANGLES */
     double alpha_i_rad[MSLICE_MAX_ANGLES]; /* incidence angle of each wavefield */
-    double psi_rad;            /* in-plane (yaw) angle: must be 0 */
+    double psi_rad;            /* in-plane (yaw) angle of the beam, |psi| < 0.1 rad: the default
+                                  probe carries the phase exp(-i k sin(psi) y) (user probes
+                                  are used as given) */
     int32_t checkpoint_every;  /* adjoint segment length in slices; <= 0 means 32 */
     uint32_t flags;            /* MSLICE_EXIT_WAVE, MSLICE_PER_STRUCTURE, MSLICE_EXACT_TRANSMISSION */
     int32_t grid_blocks;       /* launch shape: blocks of the persistent kernels, 0 = automatic

@@ -65,6 +65,7 @@ class OrcParams(ctypes.Structure):
         ("force_naive_dft", ctypes.c_int32),
         ("exit_wave", ctypes.c_int32),
         ("exact", ctypes.c_int32),
+        ("psi_rad", ctypes.c_double),
     ]
 
 
@@ -96,10 +97,11 @@ class Geometry:
     """Grid and beam: lambda, Delta, dy, dz, (Ny, Nz, Ns) and the incidence angles."""
 
     def __init__(self, ny, nz, ns, wavelength_nm=0.155, slice_nm=20.0, dy_nm=2.0,
-                 dz_nm=2.0, alpha_i_deg=(0.3,), exact_transmission=False):
+                 dz_nm=2.0, alpha_i_deg=(0.3,), exact_transmission=False, psi_deg=0.0):
         self.ny, self.nz, self.ns = int(ny), int(nz), int(ns)
         # exact 1 - n^2 in the transmission of Eq. 1 instead of 2 (delta - i beta)
         self.exact_transmission = bool(exact_transmission)
+        self.psi_rad = float(np.deg2rad(psi_deg))      # in-plane angle of the default probe
         self.wavelength_nm = float(wavelength_nm)
         self.slice_nm = float(slice_nm)
         self.dy_nm, self.dz_nm = float(dy_nm), float(dz_nm)
@@ -114,7 +116,7 @@ class Geometry:
         return OrcParams(self.wavelength_nm, self.slice_nm, self.dy_nm, self.dz_nm,
                          self.ny, self.nz, self.ns, self.nw,
                          self._alpha_keep.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
-                         int(bool(naive)), int(bool(exit_wave)), int(self.exact_transmission))
+                         int(bool(naive)), int(bool(exit_wave)), int(self.exact_transmission), self.psi_rad)
 
 
 def _c128(a, shape):

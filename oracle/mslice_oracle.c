@@ -11,9 +11,10 @@
  * What it computes (all in double precision, complex128 interleaved re/im):
  *
  *   k       = 2*pi / lambda
- *   phi_0   = user probe, or the tilted plane wave exp(-i k sin(alpha) z_l),
- *             z_l = l * dz   (Sec. 2: grazing incidence alpha_i; the probe
- *             heads toward the substrate at z index 0)
+ *   phi_0   = user probe, or the tilted plane wave
+ *             exp(-i k (sin(alpha) z_l + sin(psi) y_m)), z_l = l dz, y_m = m dy
+ *             (Sec. 2: grazing incidence alpha_i, the probe heading toward the
+ *             substrate at z index 0; in-plane angle psi)
  *   for slice j = 1 .. Ns:                                   (Eq. 1)
  *       a_j   = exp(-i k Delta (delta_j - i beta_j)) * phi_{j-1}
  *               (transmission exp((k/2i) int (1-n^2) dZ) with n = 1-delta+i beta,
@@ -71,6 +72,7 @@ typedef struct {
     int32_t force_naive_dft;  /* 1: use the O(N^2) DFT at every size */
     int32_t exit_wave;        /* 1: forward returns phi_Ns (full last propagation) instead of Psi */
     int32_t exact;            /* 1: exact 1 - n^2 in the transmission instead of 2 (delta - i beta) */
+    double psi_rad;           /* in-plane angle: the default probe also carries exp(-i k sin(psi) y) */
 } orc_params;
 
 static int is_pow2(int n) { return n >= 1 && (n & (n - 1)) == 0; }
@@ -226,10 +228,10 @@ static void initial_field(const orc_params *q, const cplx *probe, int w, cplx *p
     }
     const double k = 2.0 * M_PI / q->wavelength_nm;
     double alpha = q->alpha_i_rad ? q->alpha_i_rad[w] : 0.0;
-    for (int l = 0; l < q->nz; l++) {
-        cplx e = cexp(-I * k * sin(alpha) * ((double)l * q->dz_nm));
-        for (int m = 0; m < q->ny; m++) phi[(size_t)l * q->ny + m] = e;
-    }
+    for (int l = 0; l < q->nz; l++)
+        for (int m = 0; m < q->ny; m++)
+            phi[(size_t)l * q->ny + m] =
+                cexp(-I * k * (sin(alpha) * ((double)l * q->dz_nm) + sin(q->psi_rad) * ((double)m * q->dy_nm)));
 }
 
 /* phi <- F^-1 [ P F phi ]  (conj_p: use conj(P), the adjoint) */

@@ -23,8 +23,10 @@ struct SetupArgs {
     int ny, nz, nw;
     double slice_nm, wavelength_nm, dy_nm, dz_nm;
     double sin_alpha[MSLICE_MAX_ANGLES];
+    double sin_psi;
     float2* tab;       // Wt_y | Wt_z | P_y/ny | P_z/nz
     float2* probe_z;   // [nw][nz]
+    float2* probe_y;   // [ny] exp(-i k sin(psi) y_m)
     float2* py_out;    // optional, unnormalised
     float2* pz_out;
     float2* probe_z_out;
@@ -51,7 +53,7 @@ __device__ double2 propagator_entry(int m, int n, double d, double slice, double
 
 __global__ void k_setup(const SetupArgs S) {
     const int ny = S.ny, nz = S.nz;
-    const int total = 2 * (ny + nz) + S.nw * nz;
+    const int total = 2 * (ny + nz) + S.nw * nz + ny;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
         if (i < ny) {
             S.tab[i] = twiddle_entry(i, ny);
@@ -67,6 +69,12 @@ __global__ void k_setup(const SetupArgs S) {
             const double2 p = propagator_entry(l, nz, S.dz_nm, S.slice_nm, S.wavelength_nm);
             S.tab[i] = make_float2((float)(p.x / nz), (float)(p.y / nz));
             if (S.pz_out) S.pz_out[l] = make_float2((float)p.x, (float)p.y);
+        } else if (i >= 2 * (ny + nz) + S.nw * nz) {
+            // exp(-i k sin(psi) y_m) = exp(-i pi (2 sin(psi) m dy / lambda))
+            const int m = i - 2 * (ny + nz) - S.nw * nz;
+            double s, c;
+            sincospi(2.0 * S.sin_psi * (double)m * S.dy_nm / S.wavelength_nm, &s, &c);
+            S.probe_y[m] = make_float2((float)c, (float)(-s));
         } else {
             const int q = i - 2 * (ny + nz);
             const int w = q / nz, l = q % nz;
@@ -159,7 +167,7 @@ int validate(const mslice_params* p) {
     if (!(p->wavelength_nm > 0) || !(p->slice_nm > 0) || !(p->dy_nm > 0) || !(p->dz_nm > 0)) return MSLICE_EINVAL;
     for (int w = 0; w < p->nw; ++w)
         if (!(fabs(p->alpha_i_rad[w]) < 1.5707963)) return MSLICE_EINVAL;
-    if (p->psi_rad != 0.0) return MSLICE_EUNSUPPORTED;
+    if (!(fabs(p->psi_rad) < 0.1)) return MSLICE_EINVAL;
     if (p->flags & ~(MSLICE_EXIT_WAVE | MSLICE_PER_STRUCTURE | MSLICE_EXACT_TRANSMISSION)) return MSLICE_EINVAL;
     if (p->grid_blocks < 0 || p->col_width < 0 || p->schedule < 0 || p->schedule > 2) return MSLICE_EINVAL;
     if (p->col_width > 0 && !col_cw_ok(p->col_width, p->nz > 32 ? p->nz / 32 : 1)) return MSLICE_EINVAL;
@@ -167,7 +175,7 @@ int validate(const mslice_params* p) {
 }
 
 struct Layout {
-    size_t ctrl, partials, tab, probe_z, tvol, field, gfield, gpart, ckpt, seg, total;
+    size_t ctrl, partials, tab, probe_z, probe_y, tvol, field, gfield, gpart, ckpt, seg, total;
     int K, nseg;
 };
 
@@ -183,6 +191,7 @@ Layout make_layout(const mslice_params* p, int op) {
     L.partials = off; off = align256(off + kPartialBytes);
     L.tab = off; off = align256(off + 2 * (size_t)(p->ny + p->nz) * sizeof(float2));
     L.probe_z = off; off = align256(off + (size_t)p->nw * p->nz * sizeof(float2));
+    L.probe_y = off; off = align256(off + (size_t)p->ny * sizeof(float2));
     const size_t nvol = (p->flags & MSLICE_PER_STRUCTURE) ? (size_t)p->nw : 1;
     L.tvol = off; off = align256(off + nvol * p->ns * npx * sizeof(float2));
     L.field = off; off = align256(off + fb);
@@ -411,10 +420,12 @@ int prepare(const mslice_params* p, int op, const float* vol, const float* probe
     S.ny = p->ny; S.nz = p->nz; S.nw = p->nw;
     S.slice_nm = p->slice_nm; S.wavelength_nm = p->wavelength_nm; S.dy_nm = p->dy_nm; S.dz_nm = p->dz_nm;
     for (int i = 0; i < p->nw; ++i) S.sin_alpha[i] = sin(p->alpha_i_rad[i]);
+    S.sin_psi = sin(p->psi_rad);
     S.tab = (float2*)(w + L.tab);
     S.probe_z = (float2*)(w + L.probe_z);
+    S.probe_y = (float2*)(w + L.probe_y);
     S.py_out = py_out; S.pz_out = pz_out; S.probe_z_out = probe_z_out;
-    const int total = 2 * (p->ny + p->nz) + p->nw * p->nz;
+    const int total = 2 * (p->ny + p->nz) + p->nw * p->nz + p->ny;
     ProfRec* r = prof_begin(KID_SETUP, 0.0, st);
     k_setup<<<(total + 255) / 256, 256, 0, st>>>(S);
     prof_end(r, st);
@@ -439,6 +450,7 @@ int prepare(const mslice_params* p, int op, const float* vol, const float* probe
     a.exact = exact;
     a.probe = (const float2*)probe;
     a.probe_z = (const float2*)(w + L.probe_z);
+    a.probe_y = p->psi_rad != 0.0 ? (const float2*)(w + L.probe_y) : nullptr;
     a.tab = (const float2*)(w + L.tab);
     a.field = (float2*)(w + L.field);
     if (op != MSLICE_OP_FORWARD) {
@@ -631,10 +643,12 @@ int mslice_plan_tables(const mslice_params* p, float* py, float* pz, float* prob
     S.ny = p->ny; S.nz = p->nz; S.nw = p->nw;
     S.slice_nm = p->slice_nm; S.wavelength_nm = p->wavelength_nm; S.dy_nm = p->dy_nm; S.dz_nm = p->dz_nm;
     for (int i = 0; i < p->nw; ++i) S.sin_alpha[i] = sin(p->alpha_i_rad[i]);
+    S.sin_psi = sin(p->psi_rad);
     S.tab = (float2*)(w + L.tab);
     S.probe_z = (float2*)(w + L.probe_z);
+    S.probe_y = (float2*)(w + L.probe_y);
     S.py_out = (float2*)py; S.pz_out = (float2*)pz; S.probe_z_out = (float2*)probe_z;
-    const int total = 2 * (p->ny + p->nz) + p->nw * p->nz;
+    const int total = 2 * (p->ny + p->nz) + p->nw * p->nz + p->ny;
     k_setup<<<(total + 255) / 256, 256, 0, st>>>(S);
     return cudaGetLastError() == cudaSuccess ? MSLICE_OK : MSLICE_ELAUNCH;
 }

@@ -425,6 +425,7 @@ struct SweepArgs {
     const float2* vol;      // [ns][nz][ny] delta + i beta (read by the adjoint when exact)
     const float2* probe;    // [nw][nz][ny] or null
     const float2* probe_z;  // [nw][nz] default probe rows
+    const float2* probe_y;  // [ny] in-plane tilt of the default probe, or null (psi = 0)
     const float2* tab;      // Wt_y[ny] | Wt_z[nz] | P_y[ny]/ny | P_z[nz]/nz
     float2* field;          // [nw][nz][ny] forward state
     float2* gfield;         // [nw][nz][ny] adjoint state
@@ -528,8 +529,13 @@ __device__ void row_pass(const SweepArgs& A, const Smem& S, const int j, const b
                     for (int m = 0; m < 32; ++m) if (m < P) x[m] = __ldg(A.probe + row + t + T * m);
                 } else {
                     const float2 v = A.probe_z[(size_t)w * A.nz + z];
+                    if (A.probe_y) {
 #pragma unroll
-                    for (int m = 0; m < 32; ++m) if (m < P) x[m] = v;
+                        for (int m = 0; m < 32; ++m) if (m < P) x[m] = cmul(v, __ldg(A.probe_y + t + T * m));
+                    } else {
+#pragma unroll
+                        for (int m = 0; m < 32; ++m) if (m < P) x[m] = v;
+                    }
                 }
                 if ((A.flags & F_STORE_CKPT) && (j % A.K == 0)) {
                     float2* dst = A.ckpt + (size_t)(j / A.K) * A.nw * npx + row;

@@ -9,7 +9,8 @@ def params(geo, checkpoint_every=32, flags=0, schedule=0):
     if getattr(geo, "exact_transmission", False):
         flags |= B.MSLICE_EXACT_TRANSMISSION
     return B.make_params(geo.ny, geo.nz, geo.ns, np.rad2deg(geo.alpha_i_rad), geo.wavelength_nm,
-                         geo.slice_nm, geo.dy_nm, geo.dz_nm, checkpoint_every, flags, schedule=schedule)
+                         geo.slice_nm, geo.dy_nm, geo.dz_nm, checkpoint_every, flags, schedule=schedule,
+                         psi_rad=getattr(geo, "psi_rad", 0.0))
 
 
 def dev(a, dtype):

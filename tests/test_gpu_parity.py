@@ -61,6 +61,20 @@ def test_transmission_fp64():
     assert np.abs(t.cpu().numpy() - ref).max() < 1e-6
 
 
+@pytest.mark.parametrize("psi_deg", [0.35, -0.5])
+def test_in_plane_angle_vs_oracle(psi_deg):
+    """psi != 0: the default probe tilted in y as well; forward and gradient."""
+    geo = oracle.Geometry(128, 64, 20, alpha_i_deg=(0.2, 0.4), psi_deg=psi_deg)
+    vol = ci.random_volume(23, 128, 64, 20, scale=40)
+    I_ref = oracle.forward(geo, vol)
+    assert G.rel(G.forward(geo, vol), I_ref) <= TOL_I
+    meas = (np.sqrt(I_ref) * 1.07).astype(np.float32)
+    L_ref, g_ref = oracle.loss_grad(geo, vol, meas, 0.9)
+    L, g = G.loss_grad(geo, vol, meas, 0.9, checkpoint_every=6)
+    assert abs(L - L_ref) <= 1e-4 * abs(L_ref)
+    assert G.rel(g, g_ref) <= TOL_GRAD
+
+
 def test_exact_transmission_fp64():
     """MSLICE_EXACT_TRANSMISSION: exp((k/2i) Delta (1 - n^2)), n = 1 - delta + i beta,
     evaluated in FP64 from n."""
@@ -261,10 +275,10 @@ def test_argument_errors():
         B.mslice_forward(p, vol, None, I, None, ws[: ws.numel() // 2])
     assert e.value.code == -5
     p2 = G.params(geo)
-    p2.psi_rad = 0.01
+    p2.psi_rad = 0.2                                # in-plane angle beyond the paraxial range
     with pytest.raises(B.MsliceError) as e:
         B.mslice_forward(p2, vol, None, I, None, ws)
-    assert e.value.code == -2
+    assert e.value.code == -1
     p3 = G.params(geo)
     p3.ny = 24                                      # not a power of two
     vol3 = torch.zeros((2, 16, 24), dtype=torch.complex64, device="cuda")

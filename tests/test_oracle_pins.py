@@ -392,3 +392,16 @@ def test_coarse_map_block_index_and_snapping(oracle_lib):
     assert vol[0, 0, 0] == 0 and vol[0, 2, 0] == 0                 # outside the block
     got = oracle_lib.snap([0.2, 0.5, 0.51, -3.0, 7.0, 4.0], [0.0, 1.0, 4.0])
     np.testing.assert_array_equal(got, [0.0, 0.0, 1.0, 0.0, 4.0, 4.0])
+
+
+def test_in_plane_angle_plane_wave_lands_in_one_bin(oracle_lib):
+    """A default probe tilted in y by psi with sin(psi) = m lambda / (ny dy) is the
+    DFT basis vector of bin -m: through vacuum its far field puts all of the
+    intensity, ny nz, into detector column (ny - m) mod ny of row 0."""
+    ny, nz, m = 64, 16, 5
+    sin_psi = m * 0.155 / (ny * 2.0)
+    geo = oracle_lib.Geometry(ny, nz, 3, alpha_i_deg=(0.0,), psi_deg=np.rad2deg(np.arcsin(sin_psi)))
+    I = oracle_lib.forward(geo, np.zeros((3, nz, ny)))
+    assert I[0, 0, ny - m] == pytest.approx(ny * nz, rel=1e-12)
+    assert I.sum() == pytest.approx(ny * nz, rel=1e-12)
+    assert I[0, 0, m] < 1e-20

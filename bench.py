@@ -428,7 +428,7 @@ def run_batch(args):
                          alpha_deg=sp["alpha_deg"]))
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t0
-    bat = BatchedLossGrad(jobs, tune=not args.no_tune)
+    bat = BatchedLossGrad(jobs, tune=not args.no_tune, lanes=args.lanes)
     bat.capture()
     for _ in range(args.warmup):
         bat.replay()
@@ -454,7 +454,8 @@ def run_batch(args):
             "dtype": "f32", "data": "synthetic",
             "config": {"workload": "%d structures, grids 128-512 per axis, 128-1024 slices, 0.1-0.5 deg, "
                                    "one CUDA graph" % len(jobs),
-                       "groups": len(bat.groups), "units_per_step": bat.units, "setup_s": setup_s}}
+                       "groups": len(bat.groups), "lanes": len(bat.lanes), "units_per_step": bat.units,
+                       "setup_s": setup_s}}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -746,6 +747,7 @@ def main():
     ap.add_argument("--checkpoint", type=int, default=0,
                     help="adjoint checkpoint interval (0: keep every a_j when it fits in half the HBM, else 32)")
     ap.add_argument("--jobs", type=int, default=64)
+    ap.add_argument("--lanes", type=int, default=4, help="batch: concurrent streams, SMs split between them")
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--lr", type=float, default=2e-6)
     ap.add_argument("--max-iters", type=int, default=300)

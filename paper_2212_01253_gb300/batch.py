@@ -21,9 +21,14 @@ from . import binding as B
 
 class BatchedLossGrad:
     def __init__(self, jobs, wavelength_nm=0.155, slice_nm=20.0, dy_nm=2.0, dz_nm=2.0, checkpoint_every=32,
-                 tune=True, device="cuda"):
+                 tune=True, device="cuda", lanes=1):
         """jobs: list of dicts with 'vol' (complex64 [ns][nz][ny], CUDA), 'meas' (float32 [nz][ny], CUDA),
-        'scale' (float) and 'alpha_deg' (float)."""
+        'scale' (float) and 'alpha_deg' (float).
+
+        lanes > 1 runs the groups on that many streams at once, each group's
+        persistent kernels on SMs / lanes blocks, so that the grids of the
+        concurrent launches fit on the GPU together (one block per SM each) and
+        small groups, whose slice loops are latency-bound, overlap."""
         self.device = torch.device(device)
         groups = collections.OrderedDict()
         for i, jb in enumerate(jobs):
@@ -39,6 +44,9 @@ class BatchedLossGrad:
                                   dy_nm, dz_nm, checkpoint_every, flags=B.MSLICE_PER_STRUCTURE)
                 if tune:
                     autotune.apply(p, self.device)
+                if lanes > 1:
+                    sms = torch.cuda.get_device_properties(self.device).multi_processor_count
+                    p.grid_blocks = max(1, sms // int(lanes))
                 vols = torch.stack([jobs[i]["vol"] for i in chunk]).contiguous()
                 meas = torch.stack([jobs[i]["meas"] for i in chunk]).contiguous()
                 g = dict(p=p, vols=vols, meas=meas, scales=[float(jobs[i]["scale"]) for i in chunk],
@@ -49,12 +57,36 @@ class BatchedLossGrad:
                 self.groups.append(g)
         self.graph = None
         self.units = sum(g["p"].nw * g["p"].ny * g["p"].nz * g["p"].ns for g in self.groups)
+        # groups to lanes, longest first onto the least loaded lane (cost: work
+        # plus a per-slice latency term)
+        self.lanes = [[] for _ in range(max(1, int(lanes)))]
+        load = [0.0] * len(self.lanes)
+        cost = lambda g: g["p"].nw * g["p"].ny * g["p"].nz * g["p"].ns / 4e10 + g["p"].ns * 2.5e-5
+        for gi in sorted(range(len(self.groups)), key=lambda i: -cost(self.groups[i])):
+            k = load.index(min(load))
+            self.lanes[k].append(gi)
+            load[k] += cost(self.groups[gi])
+        self.streams = [torch.cuda.Stream(self.device) for _ in self.lanes] if len(self.lanes) > 1 else []
+
+    def _enqueue(self, g, stream=None):
+        B.mslice_loss_grad_multi(g["p"], g["vols"], None, g["meas"], g["scales"], g["loss"], g["grad"], None,
+                                 g["ws"], stream=stream)
 
     def run(self):
-        """Enqueue every group's loss and gradient on the current stream."""
-        for g in self.groups:
-            B.mslice_loss_grad_multi(g["p"], g["vols"], None, g["meas"], g["scales"], g["loss"], g["grad"], None,
-                                     g["ws"])
+        """Enqueue every group's loss and gradient: on the current stream, or
+        forked onto the lane streams and joined back into the current one."""
+        if not self.streams:
+            for g in self.groups:
+                self._enqueue(g)
+            return
+        main = torch.cuda.current_stream(self.device)
+        for st in self.streams:
+            st.wait_stream(main)
+        for st, lane in zip(self.streams, self.lanes):
+            for gi in lane:
+                self._enqueue(self.groups[gi], st)
+        for st in self.streams:
+            main.wait_stream(st)
 
     def capture(self):
         """Record run() into one CUDA graph (after one eager warm-up run)."""

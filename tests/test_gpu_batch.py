@@ -51,10 +51,13 @@ def test_batched_equals_single_and_oracle():
     assert abs(bat.loss() - total) <= 1e-9 * total
 
 
-def test_graph_replay_equals_eager():
+@pytest.mark.parametrize("lanes", [1, 3])
+def test_graph_replay_equals_eager(lanes):
+    """One CUDA graph of the whole batch, on one stream or forked onto lanes
+    (concurrent groups on a split grid), equals the eager single-stream run."""
     from paper_2212_01253_gb300.batch import BatchedLossGrad
     jobs = _jobs(2)
-    bat = BatchedLossGrad(jobs, tune=False)
+    bat = BatchedLossGrad(jobs, tune=False, lanes=lanes)
     bat.run()
     torch.cuda.synchronize()
     eager = [bat.grad(i).clone() for i in range(len(jobs))]

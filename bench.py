@@ -42,6 +42,7 @@ COUNTS = 1e6
 CKPT = 32
 METRIC = "multislice voxel-steps/s fwd+adjoint"
 UNIT = "voxel-slice-steps/s"
+HBM_BYTES_PER_UNIT = 48      # minimum HBM bytes per voxel-slice-step of loss + gradient
 
 
 def config(nw=NW, ns=NS, ckpt=CKPT):
@@ -235,6 +236,7 @@ def run_gpu(args):
     import cssi_inputs as ci
     from paper_2212_01253_gb300 import binding as B
     from paper_2212_01253_gb300 import build as cuda_build
+    from paper_2212_01253_gb300.shard import whole_job_rate
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -305,12 +307,8 @@ def run_gpu(args):
     ms = e0.elapsed_time(e1) / args.steps
     if B.mslice_status(ws) != 0:
         raise RuntimeError("device-side wait timed out in the timed region")
-    ms_t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
     units_step = NY * NZ * ns * nw
-    value = world * units_step / (ms_max / 1e3)
+    value, ms_max = whole_job_rate(units_step, ms, dev)
 
     # end to end through the public API with host buffers
     e2e = None
@@ -338,13 +336,11 @@ def run_gpu(args):
         torch.cuda.synchronize()
         if pipe.status() != 0:
             raise RuntimeError("device-side wait timed out in the end-to-end leg")
-        ems = torch.tensor([f0.elapsed_time(f1) / args.steps], dtype=torch.float64, device=dev)
-        if world > 1:
-            dist.all_reduce(ems, op=dist.ReduceOp.MAX)
-        e2e = {"value": world * units_step / (float(ems.item()) / 1e3), "unit": UNIT,
+        e_value, e_ms = whole_job_rate(units_step, f0.elapsed_time(f1) / args.steps, dev)
+        e2e = {"value": e_value, "unit": UNIT,
                "h2d_bytes_per_step": vol_pin.numel() * 8 + meas_pin.numel() * 4,
                "d2h_bytes_per_step": grad_pin[0].numel() * 8 + 8,
-               "ms_per_step": float(ems.item()),
+               "ms_per_step": e_ms,
                "api": "HostPipeline.submit (mslice_loss_grad with copies on their own streams, 2 device slots)",
                "loss_matches_device_leg": bool(abs(float(loss_pin[(args.steps - 1) % 2].item()) - float(loss.item()))
                                                <= 1e-9 * abs(float(loss.item())))}
@@ -374,6 +370,20 @@ def run_gpu(args):
                 "flops_per_unit": flops_per_unit(name)}
     kernels = {k: {"launches": v[0], "total_ms": v[1], "units": v[2]} for k, v in prof.items()}
     gpu_launches = sum(v[0] for v in prof.values())
+    # effective bandwidth of the whole step: the rate times the HBM bytes per
+    # unit that one wavefield's loss + gradient needs when the field stays on
+    # chip and the adjoint recomputes a_j from checkpoints (forward: volume 8;
+    # recompute: volume 8, a_j stored 8; adjoint: a_j reloaded 8, volume 8,
+    # gradient written 8), against the HBM copy rate.  The DRAM bytes that ncu
+    # counted for the step's two slice-loop kernels are lower: the angles share
+    # the volume and every a_j is kept, so nothing is recomputed.
+    hbm_gbs = float(peaks.get("hbm_gbs", 6800.0))
+    tf, ta = traffic_record("k_fwd"), traffic_record("k_adj")
+    eff = value * HBM_BYTES_PER_UNIT / 1e9
+    hbm = {"bytes_per_unit": HBM_BYTES_PER_UNIT, "effective": eff, "peak": hbm_gbs, "unit": "GB/s",
+           "frac": eff / hbm_gbs, "peak_basis": "measured" if "hbm_gbs" in peaks else "fallback",
+           "dram_bytes_per_unit_counted": None if tf is None or ta is None else tf + ta,
+           "dram_gbs_counted": None if tf is None or ta is None else value * (tf + ta) / 1e9}
 
     cpu = None
     if not args.no_cpu_baseline:
@@ -388,7 +398,7 @@ def run_gpu(args):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": dict(config(nw, ns, ckpt), launch_shape={"grid_blocks": p.grid_blocks, "col_width": p.col_width,
                                                          "schedule": p.schedule}),
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+            "roofline": roofline, "effective_hbm": hbm, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
             "gpu_launches": gpu_launches, "kernels": kernels, "loss": float(loss.item())}
     print(json.dumps(line), flush=True)
     if world > 1:
@@ -402,17 +412,31 @@ def run_gpu(args):
 def run_batch(args):
     """64 independent structures of uneven shape (grids 128..512 per axis,
     128..1024 slices, 0.1-0.5 deg), loss + gradient of all of them as one
-    CUDA-graph launch; voxel-slice-steps/s over the whole batch."""
+    CUDA-graph launch; voxel-slice-steps/s over the whole batch.  Under
+    torchrun the structures are split between the ranks by index (strong
+    scaling: the batch is fixed)."""
     import torch
+    import torch.distributed as dist
 
     import cssi_inputs as ci
     from paper_2212_01253_gb300 import binding as B
     from paper_2212_01253_gb300 import build as cuda_build
     from paper_2212_01253_gb300.batch import BatchedLossGrad
+    from paper_2212_01253_gb300.shard import shard, whole_job_rate
 
-    cuda_build.build()
-    torch.cuda.set_device(0)
-    specs = ci.batched_jobs(0, args.jobs)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    if rank == 0 or not os.path.exists(cuda_build.LIB):
+        cuda_build.build()
+    if world > 1:
+        dist.barrier()
+    all_specs = ci.batched_jobs(0, args.jobs)
+    specs = [all_specs[i] for i in shard(len(all_specs), rank, world)]
     jobs = []
     t0 = time.perf_counter()
     for k, sp in enumerate(specs):
@@ -433,14 +457,18 @@ def run_batch(args):
     for _ in range(args.warmup):
         bat.replay()
     torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     for _ in range(args.steps):
         bat.replay()
     e1.record()
     torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
     bat.check()
-    ms = e0.elapsed_time(e1) / args.steps
+    value, ms = whole_job_rate(bat.units, e0.elapsed_time(e1) / args.steps, dev)
     # the same batch as eager per-group calls (no graph) for comparison
     f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     f0.record()
@@ -448,15 +476,21 @@ def run_batch(args):
         bat.run()
     f1.record()
     torch.cuda.synchronize()
-    line = {"metric": "batched multislice voxel-steps/s fwd+adjoint", "value": bat.units / (ms / 1e3),
-            "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
-            "eager_ms_per_step": f0.elapsed_time(f1) / args.steps, "higher_is_better": True,
+    eager_ms = f0.elapsed_time(f1) / args.steps
+    if rank != 0:
+        dist.destroy_process_group()
+        return 0
+    line = {"metric": "batched multislice voxel-steps/s fwd+adjoint", "value": value,
+            "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "eager_ms_per_step": eager_ms, "higher_is_better": True, "scaling": "strong",
             "dtype": "f32", "data": "synthetic",
             "config": {"workload": "%d structures, grids 128-512 per axis, 128-1024 slices, 0.1-0.5 deg, "
-                                   "one CUDA graph" % len(jobs),
-                       "groups": len(bat.groups), "lanes": len(bat.lanes), "units_per_step": bat.units,
-                       "setup_s": setup_s}}
+                                   "one CUDA graph per rank" % len(all_specs),
+                       "structures_rank0": len(jobs), "groups_rank0": len(bat.groups), "lanes": len(bat.lanes),
+                       "units_per_step_rank0": bat.units, "setup_s": setup_s}}
     print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
     return 0
 
 

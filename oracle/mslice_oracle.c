@@ -29,6 +29,16 @@
  *   I       = |Psi|^2
  *   L       = sum (sqrt(s I) - m)^2   (Eq. 4 on amplitudes, without the 1/N)
  *
+ * With `strang` the splitting is symmetric instead of transmission-first:
+ * half a step of free propagation, then per slice the transmission and a full
+ * step, the last step being a half step again:
+ *   phi_0' = F^-1 [ exp(-i (Delta/2) (k_y^2 + k_z^2) / 2k) * F phi_0 ]
+ *   the loop above from phi_0'; the exit wave phi_Ns = U(Delta/2) a_Ns.
+ * The far field omits that final half step as it omits the full one (a
+ * unit-modulus Fourier phase), so I, L and the adjoint are the loop above
+ * started from phi_0'.  Over slices of uniform content this is second order
+ * in Delta; the transmission-first form is first order.
+ *
  *   k_y = 2*pi*fftfreq(Ny, dy), k_z = 2*pi*fftfreq(Nz, dz); forward DFT kernel
  *   e^{-i}; natural (unshifted) frequency order.
  *
@@ -73,6 +83,7 @@ typedef struct {
     int32_t exit_wave;        /* 1: forward returns phi_Ns (full last propagation) instead of Psi */
     int32_t exact;            /* 1: exact 1 - n^2 in the transmission instead of 2 (delta - i beta) */
     double psi_rad;           /* in-plane angle: the default probe also carries exp(-i k sin(psi) y) */
+    int32_t strang;           /* 1: symmetric splitting (half steps of propagation at both ends) */
 } orc_params;
 
 static int is_pow2(int n) { return n >= 1 && (n & (n - 1)) == 0; }
@@ -183,9 +194,10 @@ static double angular_freq(int m, int n, double d)
     return 2.0 * M_PI * (double)f / ((double)n * d);
 }
 
-/* Fresnel propagator of Eq. 1 on the full 2-D frequency grid:
- * P[l][m] = exp(-i Delta (k_y[m]^2 + k_z[l]^2) / (2k)). */
-static cplx *make_propagator(const orc_params *q)
+/* Fresnel propagator of Eq. 1 on the full 2-D frequency grid over a distance
+ * len (Delta, or Delta/2 for the half steps of the symmetric splitting):
+ * P[l][m] = exp(-i len (k_y[m]^2 + k_z[l]^2) / (2k)). */
+static cplx *make_propagator(const orc_params *q, double len)
 {
     const int ny = q->ny, nz = q->nz;
     const double k = 2.0 * M_PI / q->wavelength_nm;
@@ -195,7 +207,7 @@ static cplx *make_propagator(const orc_params *q)
         double kz = angular_freq(l, nz, q->dz_nm);
         for (int m = 0; m < ny; m++) {
             double ky = angular_freq(m, ny, q->dy_nm);
-            P[(size_t)l * ny + m] = cexp(-I * q->slice_nm * (ky * ky + kz * kz) / (2.0 * k));
+            P[(size_t)l * ny + m] = cexp(-I * len * (ky * ky + kz * kz) / (2.0 * k));
         }
     }
     return P;
@@ -248,12 +260,13 @@ static void propagate(const plan2 *p, const cplx *P, cplx *phi, int conj_p)
 /* Runs the slice loop for wavefield w.  If a_store is non-NULL, stores a_j
  * for every slice ([ns][nz][ny]).  On return `out` holds Psi (far field,
  * unitary DFT of a_Ns) or, with exit_wave, phi_Ns. */
-static void forward_one(const orc_params *q, const plan2 *p, const cplx *P, const cplx *vol,
-                        const cplx *probe, int w, cplx *phi, cplx *a_store, cplx *out)
+static void forward_one(const orc_params *q, const plan2 *p, const cplx *P, const cplx *Ph,
+                        const cplx *vol, const cplx *probe, int w, cplx *phi, cplx *a_store, cplx *out)
 {
     const size_t npx = (size_t)q->ny * q->nz;
     const double kd = (2.0 * M_PI / q->wavelength_nm) * q->slice_nm;
     initial_field(q, probe, w, phi);
+    if (q->strang) propagate(p, Ph, phi, 0);
     for (int j = 0; j < q->ns; j++) {
         const cplx *v = vol + (size_t)j * npx;
 #pragma omp parallel for schedule(static)
@@ -262,7 +275,7 @@ static void forward_one(const orc_params *q, const plan2 *p, const cplx *P, cons
         if (j < q->ns - 1) propagate(p, P, phi, 0);
     }
     if (q->exit_wave) {
-        propagate(p, P, phi, 0);
+        propagate(p, q->strang ? Ph : P, phi, 0);
         memcpy(out, phi, sizeof(cplx) * npx);
     } else {
         memcpy(out, phi, sizeof(cplx) * npx);
@@ -320,12 +333,13 @@ int orc_forward(const orc_params *q, const double *vol, const double *probe,
     if (check(q) || !vol) return ORC_EINVAL;
     const size_t npx = (size_t)q->ny * q->nz;
     plan2 p;
-    cplx *P = make_propagator(q);
+    cplx *P = make_propagator(q, q->slice_nm);
+    cplx *Ph = q->strang ? make_propagator(q, 0.5 * q->slice_nm) : NULL;
     cplx *phi = (cplx *)malloc(sizeof(cplx) * npx), *out = (cplx *)malloc(sizeof(cplx) * npx);
     int rc = plan_init(&p, q->ny, q->nz, q->force_naive_dft);
-    if (rc || !P || !phi || !out) { rc = ORC_ENOMEM; goto done; }
+    if (rc || !P || (q->strang && !Ph) || !phi || !out) { rc = ORC_ENOMEM; goto done; }
     for (int w = 0; w < q->nw; w++) {
-        forward_one(q, &p, P, (const cplx *)vol, (const cplx *)probe, w, phi, NULL, out);
+        forward_one(q, &p, P, Ph, (const cplx *)vol, (const cplx *)probe, w, phi, NULL, out);
         if (field_out) memcpy((cplx *)field_out + (size_t)w * npx, out, sizeof(cplx) * npx);
         if (intensity)
             for (size_t i = 0; i < npx; i++) {
@@ -334,7 +348,7 @@ int orc_forward(const orc_params *q, const double *vol, const double *probe,
             }
     }
 done:
-    plan_free(&p); free(P); free(phi); free(out);
+    plan_free(&p); free(P); free(Ph); free(phi); free(out);
     return rc;
 }
 
@@ -374,19 +388,20 @@ int orc_adjoint(const orc_params *q, const double *vol, const double *probe,
     if (check(q) || q->exit_wave || !vol || !g_psi || !grad) return ORC_EINVAL;
     const size_t npx = (size_t)q->ny * q->nz;
     plan2 p;
-    cplx *P = make_propagator(q);
+    cplx *P = make_propagator(q, q->slice_nm);
+    cplx *Ph = q->strang ? make_propagator(q, 0.5 * q->slice_nm) : NULL;
     cplx *phi = (cplx *)malloc(sizeof(cplx) * npx), *out = (cplx *)malloc(sizeof(cplx) * npx);
     cplx *a = (cplx *)malloc(sizeof(cplx) * npx * (size_t)q->ns);
     int rc = plan_init(&p, q->ny, q->nz, q->force_naive_dft);
-    if (rc || !P || !phi || !out || !a) { rc = ORC_ENOMEM; goto done; }
+    if (rc || !P || (q->strang && !Ph) || !phi || !out || !a) { rc = ORC_ENOMEM; goto done; }
     memset(grad, 0, sizeof(cplx) * npx * (size_t)q->ns);
     for (int w = 0; w < q->nw; w++) {
-        forward_one(q, &p, P, (const cplx *)vol, (const cplx *)probe, w, phi, a, out);
+        forward_one(q, &p, P, Ph, (const cplx *)vol, (const cplx *)probe, w, phi, a, out);
         memcpy(phi, (const cplx *)g_psi + (size_t)w * npx, sizeof(cplx) * npx);
         adjoint_one(q, &p, P, (const cplx *)vol, a, phi, grad);
     }
 done:
-    plan_free(&p); free(P); free(phi); free(out); free(a);
+    plan_free(&p); free(P); free(Ph); free(phi); free(out); free(a);
     return rc;
 }
 
@@ -399,15 +414,16 @@ int orc_loss_grad(const orc_params *q, const double *vol, const double *probe,
     if (check(q) || q->exit_wave || !vol || !meas_amp || !loss || !grad || !(scale > 0)) return ORC_EINVAL;
     const size_t npx = (size_t)q->ny * q->nz;
     plan2 p;
-    cplx *P = make_propagator(q);
+    cplx *P = make_propagator(q, q->slice_nm);
+    cplx *Ph = q->strang ? make_propagator(q, 0.5 * q->slice_nm) : NULL;
     cplx *phi = (cplx *)malloc(sizeof(cplx) * npx), *psi = (cplx *)malloc(sizeof(cplx) * npx);
     cplx *a = (cplx *)malloc(sizeof(cplx) * npx * (size_t)q->ns);
     int rc = plan_init(&p, q->ny, q->nz, q->force_naive_dft);
-    if (rc || !P || !phi || !psi || !a) { rc = ORC_ENOMEM; goto done; }
+    if (rc || !P || (q->strang && !Ph) || !phi || !psi || !a) { rc = ORC_ENOMEM; goto done; }
     memset(grad, 0, sizeof(cplx) * npx * (size_t)q->ns);
     double L = 0.0;
     for (int w = 0; w < q->nw; w++) {
-        forward_one(q, &p, P, (const cplx *)vol, (const cplx *)probe, w, phi, a, psi);
+        forward_one(q, &p, P, Ph, (const cplx *)vol, (const cplx *)probe, w, phi, a, psi);
         const double *m = meas_amp + (size_t)w * npx;
         for (size_t i = 0; i < npx; i++) {
             double I2 = creal(psi[i]) * creal(psi[i]) + cimag(psi[i]) * cimag(psi[i]);
@@ -420,6 +436,6 @@ int orc_loss_grad(const orc_params *q, const double *vol, const double *probe,
     }
     *loss = L;
 done:
-    plan_free(&p); free(P); free(phi); free(psi); free(a);
+    plan_free(&p); free(P); free(Ph); free(phi); free(psi); free(a);
     return rc;
 }

@@ -247,6 +247,53 @@ def test_slice_thickness_convergence(oracle_lib):
     assert diffs[1] < diffs[0] and diffs[2] < diffs[1]
 
 
+def _paraxial_exact(nz, dz, w, probe, length):
+    """exp(L (K + V)) phi0 for a medium uniform along the beam (ny = 1): the
+    paraxial equation's generator is K = F^-1 diag(-i k_z^2 / 2k) F plus
+    V = diag(-i k (delta - i beta)), exponentiated as a dense matrix."""
+    import scipy.linalg
+    kz = 2 * np.pi * np.fft.fftfreq(nz, dz)
+    F = np.fft.fft(np.eye(nz), axis=0)
+    Kop = np.linalg.solve(F, np.diag(-1j * kz ** 2 / (2 * K)) @ F)
+    Vop = np.diag(-1j * K * np.conj(w))
+    return scipy.linalg.expm(length * (Kop + Vop)) @ probe
+
+
+@pytest.mark.parametrize("strang,order", [(False, 1), (True, 2)])
+def test_splitting_order_against_the_matrix_exponential(oracle_lib, strang, order):
+    """In a medium uniform along the beam the slices are exact, so the exit
+    wave differs from exp(L (K + V)) phi0 only by the splitting: halving Delta
+    halves the error of the transmission-first form and quarters that of the
+    symmetric form.  A half step put in the wrong place or left out drops the
+    symmetric form back to first order."""
+    nz, dz, length = 32, 2.0, 2560.0
+    z = np.arange(nz) * dz
+    bump = np.exp(-((z - 32.0) / 10.0) ** 2)
+    w = 4e-5 * bump + 2e-6j * bump
+    probe = np.exp(-((z - 24.0) / 8.0) ** 2).astype(np.complex128)
+    exact = _paraxial_exact(nz, dz, w, probe, length)
+    errs = []
+    for ns in (8, 16, 32, 64):
+        geo = oracle_lib.Geometry(1, nz, ns, slice_nm=length / ns, dz_nm=dz, alpha_i_deg=(0.0,), strang=strang)
+        vol = np.broadcast_to(w[None, :, None], (ns, nz, 1)).copy()
+        out = oracle_lib.forward(geo, vol, probe=probe.reshape(1, nz, 1), exit_wave=True)[0, :, 0]
+        errs.append(rel(out, exact))
+    ratios = np.array(errs[:-1]) / np.array(errs[1:])
+    assert np.all(np.abs(ratios - 2 ** order) < 0.1), ratios
+    assert errs[-1] < (1e-4 if strang else 2e-2)
+
+
+def test_symmetric_splitting_in_free_space_is_the_full_propagation(oracle_lib):
+    """With delta = beta = 0 both splittings propagate the exit wave over
+    Ns Delta exactly: the symmetric form's two half steps make one full step."""
+    ny, nz, ns = 16, 32, 5
+    probe = ci.gaussian_probe(ny, nz, 2.0, 2.0, 6.0)[None]
+    vol = np.zeros((ns, nz, ny), np.complex128)
+    outs = [oracle_lib.forward(oracle_lib.Geometry(ny, nz, ns, alpha_i_deg=(0.0,), strang=st), vol,
+                               probe=probe, exit_wave=True) for st in (False, True)]
+    assert np.abs(outs[0] - outs[1]).max() < 1e-13
+
+
 # --------------------------------------------------------------------------
 # Gradient: central finite differences and the transpose identity
 # --------------------------------------------------------------------------
@@ -284,11 +331,11 @@ def test_exact_transmission_from_refractive_index(oracle_lib):
     assert abs(np.angle(np.exp(k / 2j * 20.0 * (1 - n * n)) / np.exp(-1j * k * 20.0 * (delta - 1j * beta)))) > 1e-3
 
 
-@pytest.mark.parametrize("exact", [False, True])
-def test_gradient_central_differences(oracle_lib, exact):
+@pytest.mark.parametrize("exact,strang", [(False, False), (True, False), (False, True)])
+def test_gradient_central_differences(oracle_lib, exact, strang):
     """dL/ddelta and dL/dbeta on a 16x16x8 sub-volume of a 32x32x16 grid."""
     ny, nz, ns = 32, 32, 16
-    geo = oracle_lib.Geometry(ny, nz, ns, alpha_i_deg=(0.3,), exact_transmission=exact)
+    geo = oracle_lib.Geometry(ny, nz, ns, alpha_i_deg=(0.3,), exact_transmission=exact, strang=strang)
     vol = ci.random_volume(11, ny, nz, ns, scale=40).astype(np.complex128)
     probe = ci.random_probe(11, 1, ny, nz).astype(np.complex128)
     I0 = oracle_lib.forward(geo, vol, probe=probe)

@@ -79,6 +79,16 @@ extern "C" {
                                          (w - w^2/2)) instead of the linearised
                                          exp(-i k Delta w); the gradient follows
                                          (d log t / dw = -i k Delta (1 - w)) */
+#define MSLICE_STRANG 8u  /* symmetric splitting of Eq. 1's slice step: half a
+                             step of free propagation (Delta/2) before the first
+                             slice; with MSLICE_EXIT_WAVE the last propagation is
+                             a half step too.  The far field omits that final half
+                             step (a unit-modulus phase on the detector), so I,
+                             the loss and the gradient are those of the default
+                             transmission-first loop started from
+                             F^-1 P(Delta/2) F phi_0.  Second order in Delta
+                             over slices of uniform content; the default is
+                             first order.  Costs one extra slice-loop launch. */
 
 typedef struct mslice_params {
     double wavelength_nm;      /* lambda; k = 2 pi / lambda is formed in FP64 */
@@ -93,7 +103,8 @@ typedef struct mslice_params {
                                   probe carries the phase exp(-i k sin(psi) y) (user probes
                                   are used as given) */
     int32_t checkpoint_every;  /* adjoint segment length in slices; <= 0 means 32 */
-    uint32_t flags;            /* MSLICE_EXIT_WAVE, MSLICE_PER_STRUCTURE, MSLICE_EXACT_TRANSMISSION */
+    uint32_t flags;            /* MSLICE_EXIT_WAVE, MSLICE_PER_STRUCTURE, MSLICE_EXACT_TRANSMISSION,
+                                  MSLICE_STRANG */
     int32_t grid_blocks;       /* launch shape: blocks of the persistent kernels, 0 = automatic
                                   (capped at the co-resident maximum) */
     int32_t col_width;         /* launch shape: columns per column-pass group (4, 8 or 16),

@@ -22,6 +22,7 @@ MSLICE_OP_FORWARD, MSLICE_OP_ADJOINT, MSLICE_OP_LOSS_GRAD = 0, 1, 2
 MSLICE_EXIT_WAVE = 1
 MSLICE_PER_STRUCTURE = 2
 MSLICE_EXACT_TRANSMISSION = 4
+MSLICE_STRANG = 8
 ERRORS = {-1: "MSLICE_EINVAL", -2: "MSLICE_EUNSUPPORTED", -3: "MSLICE_ELAUNCH",
           -4: "MSLICE_ETIMEDOUT", -5: "MSLICE_EWORKSPACE"}
 

@@ -25,6 +25,7 @@ struct SetupArgs {
     double sin_alpha[MSLICE_MAX_ANGLES];
     double sin_psi;
     float2* tab;       // Wt_y | Wt_z | P_y/ny | P_z/nz
+    float2* tab_half;  // the same with P over Delta/2, or null
     float2* probe_z;   // [nw][nz]
     float2* probe_y;   // [ny] exp(-i k sin(psi) y_m)
     float2* py_out;    // optional, unnormalised
@@ -57,18 +58,28 @@ __global__ void k_setup(const SetupArgs S) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
         if (i < ny) {
             S.tab[i] = twiddle_entry(i, ny);
+            if (S.tab_half) S.tab_half[i] = S.tab[i];
         } else if (i < ny + nz) {
             S.tab[i] = twiddle_entry(i - ny, nz);
+            if (S.tab_half) S.tab_half[i] = S.tab[i];
         } else if (i < 2 * ny + nz) {
             const int m = i - ny - nz;
             const double2 p = propagator_entry(m, ny, S.dy_nm, S.slice_nm, S.wavelength_nm);
             S.tab[i] = make_float2((float)(p.x / ny), (float)(p.y / ny));
             if (S.py_out) S.py_out[m] = make_float2((float)p.x, (float)p.y);
+            if (S.tab_half) {
+                const double2 h = propagator_entry(m, ny, S.dy_nm, 0.5 * S.slice_nm, S.wavelength_nm);
+                S.tab_half[i] = make_float2((float)(h.x / ny), (float)(h.y / ny));
+            }
         } else if (i < 2 * (ny + nz)) {
             const int l = i - 2 * ny - nz;
             const double2 p = propagator_entry(l, nz, S.dz_nm, S.slice_nm, S.wavelength_nm);
             S.tab[i] = make_float2((float)(p.x / nz), (float)(p.y / nz));
             if (S.pz_out) S.pz_out[l] = make_float2((float)p.x, (float)p.y);
+            if (S.tab_half) {
+                const double2 h = propagator_entry(l, nz, S.dz_nm, 0.5 * S.slice_nm, S.wavelength_nm);
+                S.tab_half[i] = make_float2((float)(h.x / nz), (float)(h.y / nz));
+            }
         } else if (i >= 2 * (ny + nz) + S.nw * nz) {
             // exp(-i k sin(psi) y_m) = exp(-i pi (2 sin(psi) m dy / lambda))
             const int m = i - 2 * (ny + nz) - S.nw * nz;
@@ -168,14 +179,17 @@ int validate(const mslice_params* p) {
     for (int w = 0; w < p->nw; ++w)
         if (!(fabs(p->alpha_i_rad[w]) < 1.5707963)) return MSLICE_EINVAL;
     if (!(fabs(p->psi_rad) < 0.1)) return MSLICE_EINVAL;
-    if (p->flags & ~(MSLICE_EXIT_WAVE | MSLICE_PER_STRUCTURE | MSLICE_EXACT_TRANSMISSION)) return MSLICE_EINVAL;
+    if (p->flags & ~(MSLICE_EXIT_WAVE | MSLICE_PER_STRUCTURE | MSLICE_EXACT_TRANSMISSION | MSLICE_STRANG))
+        return MSLICE_EINVAL;
     if (p->grid_blocks < 0 || p->col_width < 0 || p->schedule < 0 || p->schedule > 2) return MSLICE_EINVAL;
     if (p->col_width > 0 && !col_cw_ok(p->col_width, p->nz > 32 ? p->nz / 32 : 1)) return MSLICE_EINVAL;
     return MSLICE_OK;
 }
 
 struct Layout {
-    size_t ctrl, partials, tab, probe_z, probe_y, tvol, field, gfield, gpart, ckpt, seg, total;
+    size_t ctrl, partials, tab, probe_z, probe_y, tvol, field, gfield, gpart, ckpt, seg;
+    size_t tab_half, probe_half, zero_t;  // symmetric splitting only (0 otherwise)
+    size_t total;
     int K, nseg;
 };
 
@@ -195,6 +209,11 @@ Layout make_layout(const mslice_params* p, int op) {
     const size_t nvol = (p->flags & MSLICE_PER_STRUCTURE) ? (size_t)p->nw : 1;
     L.tvol = off; off = align256(off + nvol * p->ns * npx * sizeof(float2));
     L.field = off; off = align256(off + fb);
+    if (p->flags & MSLICE_STRANG) {
+        L.tab_half = off; off = align256(off + 2 * (size_t)(p->ny + p->nz) * sizeof(float2));
+        L.probe_half = off; off = align256(off + fb);
+        L.zero_t = off; off = align256(off + npx * sizeof(float2));
+    }
     if (op == MSLICE_OP_ADJOINT || op == MSLICE_OP_LOSS_GRAD) {
         L.gfield = off; off = align256(off + fb);
         L.gpart = off; off = align256(off + (p->nw > 1 && !(p->flags & MSLICE_PER_STRUCTURE)
@@ -394,6 +413,7 @@ struct Plan {
     size_t smem;
     int grid;
     SweepArgs base;
+    const float2* tab_half;  // P over Delta/2 (symmetric splitting), else null
 };
 
 int prepare(const mslice_params* p, int op, const float* vol, const float* probe, void* ws, size_t ws_bytes,
@@ -422,6 +442,8 @@ int prepare(const mslice_params* p, int op, const float* vol, const float* probe
     for (int i = 0; i < p->nw; ++i) S.sin_alpha[i] = sin(p->alpha_i_rad[i]);
     S.sin_psi = sin(p->psi_rad);
     S.tab = (float2*)(w + L.tab);
+    const bool strang = (p->flags & MSLICE_STRANG) != 0;
+    S.tab_half = strang ? (float2*)(w + L.tab_half) : nullptr;
     S.probe_z = (float2*)(w + L.probe_z);
     S.probe_y = (float2*)(w + L.probe_y);
     S.py_out = py_out; S.pz_out = pz_out; S.probe_z_out = probe_z_out;
@@ -468,6 +490,27 @@ int prepare(const mslice_params* p, int op, const float* vol, const float* probe
     a.per_w = (p->flags & MSLICE_PER_STRUCTURE) ? 1 : 0;
     a.lcw = ilog2(cw);
     a.split = p->nw >= 2 && p->schedule == 2;
+    P->tab_half = nullptr;
+    if (strang) {
+        // symmetric splitting: phi_0' = F^-1 P(Delta/2) F phi_0 for every
+        // wavefield, by the forward slice loop over one slice of vacuum
+        // (u = t - 1 = 0, so a = phi exactly) with the half-step tables; the
+        // slice loops then start from phi_0' as from a user probe
+        if (note(cudaMemsetAsync(w + L.zero_t, 0, (size_t)p->ny * p->nz * sizeof(float2), st), "cudaMemsetAsync"))
+            return MSLICE_ELAUNCH;
+        P->tab_half = (const float2*)(w + L.tab_half);
+        SweepArgs h = a;
+        h.tvol = (const float2*)(w + L.zero_t);
+        h.per_w = 0;
+        h.tab = P->tab_half;
+        h.field = (float2*)(w + L.probe_half);
+        h.j_begin = 0; h.j_end = 1;
+        h.prop_last = 1;
+        h.flags = 0;
+        rc = launch_coop(P->ks.fwd, P->grid, P->smem, h, st, KID_FWD, (double)p->nw * p->ny * p->nz);
+        if (rc) return rc;
+        a.probe = (const float2*)(w + L.probe_half);
+    }
     return MSLICE_OK;
 }
 
@@ -556,8 +599,10 @@ int mslice_forward(const mslice_params* p, const float* vol, const float* probe,
         if ((rc = launch_coop(P.ks.fwd, P.grid, P.smem, a, st, KID_FWD, u * (p->ns - 1)))) return rc;
     }
     a.j_end = p->ns;
-    if (p->flags & MSLICE_EXIT_WAVE)
+    if (p->flags & MSLICE_EXIT_WAVE) {
+        if (P.tab_half) a.tab = P.tab_half;   // the last propagation is a half step
         return launch_coop((const void*)k_last<C_EXIT>, P.grid, P.smem, a, st, KID_LAST, u);
+    }
     return launch_coop((const void*)k_last<C_FAR>, P.grid, P.smem, a, st, KID_LAST, u);
 }
 

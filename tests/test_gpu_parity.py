@@ -109,6 +109,67 @@ def test_exact_transmission_loss_grad_vs_oracle(ny, nz, ns, nw, K):
 
 
 # --------------------------------------------------------------------------
+# symmetric splitting (MSLICE_STRANG): half steps of propagation at both ends
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("ny,nz,ns,nw,user_probe", [(64, 64, 12, 2, False), (32, 128, 1, 1, True),
+                                                     (256, 64, 7, 3, False), (64, 32, 5, 1, True)])
+def test_strang_forward_and_exit_wave_vs_oracle(ny, nz, ns, nw, user_probe):
+    angles = np.linspace(0.15, 0.45, nw)
+    geo = oracle.Geometry(ny, nz, ns, alpha_i_deg=angles, strang=True)
+    vol = ci.random_volume(ny + 3 * ns, ny, nz, ns, scale=60)
+    probe = ci.random_probe(ny + ns, nw, ny, nz) if user_probe else None
+    I_ref = oracle.forward(geo, vol, probe=probe)
+    I = G.forward(geo, vol, probe=probe)
+    assert G.rel(I, I_ref) <= TOL_I
+    ex_ref = oracle.forward(geo, vol, probe=probe, exit_wave=True)
+    ex = G.forward(geo, vol, probe=probe, exit_wave=True)
+    assert G.rel(ex, ex_ref) <= TOL_I
+    # the transmission-first result is far outside the tolerance
+    lie = oracle.Geometry(ny, nz, ns, alpha_i_deg=angles)
+    assert G.rel(I, oracle.forward(lie, vol, probe=probe)) > 10 * TOL_I
+    assert G.rel(ex, oracle.forward(lie, vol, probe=probe, exit_wave=True)) > 10 * TOL_I
+
+
+@pytest.mark.parametrize("ny,nz,ns,nw,K,schedule", [(64, 64, 24, 1, 5, 0), (32, 64, 13, 3, 4, 0),
+                                                    (64, 128, 16, 4, 16, 2)])
+def test_strang_loss_grad_vs_oracle(ny, nz, ns, nw, K, schedule):
+    geo = oracle.Geometry(ny, nz, ns, alpha_i_deg=np.linspace(0.15, 0.45, nw), strang=True)
+    vol = ci.random_volume(2 * ny + ns, ny, nz, ns, scale=60)
+    meas = _target(geo, vol.astype(np.complex128) * 1.1, 5)
+    L_ref, g_ref, I_ref = oracle.loss_grad(geo, vol, meas, 0.7, return_intensity=True)
+    L, g, I = G.loss_grad(geo, vol, meas, 0.7, checkpoint_every=K, return_intensity=True, schedule=schedule)
+    assert G.rel(I, I_ref) <= TOL_I
+    assert abs(L - L_ref) <= 1e-4 * abs(L_ref)
+    assert G.rel(g, g_ref) <= TOL_GRAD
+
+
+def test_strang_per_structure_vs_oracle():
+    """mslice_loss_grad_multi with MSLICE_STRANG: each structure's half-step
+    probe is its own default probe propagated by Delta/2."""
+    from paper_2212_01253_gb300 import binding as B
+    ny, nz, ns, nw = 64, 64, 9, 3
+    angles = (0.2, 0.3, 0.4)
+    vols = [ci.random_volume(300 + i, ny, nz, ns, scale=60) for i in range(nw)]
+    geos = [oracle.Geometry(ny, nz, ns, alpha_i_deg=(a,), strang=True) for a in angles]
+    meas = [_target(g, v.astype(np.complex128) * 1.1, 7 + i) for i, (g, v) in enumerate(zip(geos, vols))]
+    scales = [0.7, 1.1, 0.9]
+    p = B.make_params(ny, nz, ns, angles, checkpoint_every=4, flags=B.MSLICE_PER_STRUCTURE | B.MSLICE_STRANG)
+    ws = B.workspace(p, B.MSLICE_OP_LOSS_GRAD)
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    grad = torch.empty((nw, ns, nz, ny), dtype=torch.complex64, device="cuda")
+    B.mslice_loss_grad_multi(p, G.dev(np.stack(vols), np.complex64), None,
+                             G.dev(np.concatenate(meas), np.float32), scales, loss, grad, None, ws)
+    torch.cuda.synchronize()
+    assert B.mslice_status(ws) == 0
+    L_ref = 0.0
+    for i in range(nw):
+        Li, gi = oracle.loss_grad(geos[i], vols[i], meas[i], scales[i])
+        L_ref += Li
+        assert G.rel(grad[i].cpu().numpy(), gi) <= TOL_GRAD
+    assert abs(float(loss.item()) - L_ref) <= 1e-4 * abs(L_ref)
+
+
+# --------------------------------------------------------------------------
 # forward parity
 # --------------------------------------------------------------------------
 @pytest.mark.parametrize("seed", range(10))

@@ -755,6 +755,61 @@ def run_learned(args):
     return 0
 
 
+def run_convergence(args):
+    """Slice-thickness convergence: one structure 10 um long along the beam
+    (Si substrate + 20 Au boxes sized in nm, each slice holding its thickness
+    average), cut into slices of 200 down to 5 nm.  Far-field intensities at
+    three incidence angles, with the transmission-first and the symmetric
+    splitting, against the symmetric splitting at 2.5 nm; forward time per
+    thickness."""
+    import torch
+
+    import cssi_inputs as ci
+    from paper_2212_01253_gb300 import binding as B
+    from paper_2212_01253_gb300 import build as cuda_build
+
+    cuda_build.build()
+    torch.cuda.set_device(0)
+    ny = nz = 256
+    length = 10000.0
+    ang = (0.15, 0.3, 0.5)
+    boxes = ci.boxes_nm(0, ny, nz, length)
+
+    def forward(delta, flags):
+        vol = torch.from_numpy(ci.slice_boxes(boxes, ny, nz, length, delta)).cuda()
+        p = B.make_params(ny, nz, vol.shape[0], ang, slice_nm=delta, flags=flags)
+        ws = B.workspace(p, B.MSLICE_OP_FORWARD)
+        inten = torch.empty((len(ang), nz, ny), dtype=torch.float32, device="cuda")
+        for _ in range(args.warmup):
+            B.mslice_forward(p, vol, None, inten, None, ws)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            B.mslice_forward(p, vol, None, inten, None, ws)
+        e1.record()
+        torch.cuda.synchronize()
+        if B.mslice_status(ws) != 0:
+            raise RuntimeError("device-side wait timed out")
+        return inten.double().cpu().numpy(), e0.elapsed_time(e1) / args.steps, vol.shape[0]
+
+    I_ref, ms_ref, ns_ref = forward(2.5, B.MSLICE_STRANG)
+    rows = []
+    for delta in (200.0, 100.0, 50.0, 20.0, 10.0, 5.0):
+        for name, flags in (("transmission-first", 0), ("symmetric", B.MSLICE_STRANG)):
+            I, ms, ns = forward(delta, flags)
+            err = [float(np.linalg.norm(I[w] - I_ref[w]) / np.linalg.norm(I_ref[w])) for w in range(len(ang))]
+            rows.append({"slice_nm": delta, "slices": ns, "splitting": name, "rel_l2_per_angle": err,
+                         "ms_forward": ms})
+    line = {"metric": "far-field intensity error vs slice thickness", "unit": "relative L2", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "256x256 grid (2 nm), 10 um along the beam, Si + 20 Au boxes, "
+                                   "angles 0.15/0.3/0.5 deg; reference: symmetric splitting at 2.5 nm "
+                                   "(%d slices, %.2f ms per forward)" % (ns_ref, ms_ref)},
+            "rows": rows}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -767,10 +822,11 @@ def main():
     ap.add_argument("--cpu-angles", type=int, default=3)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="sweep", choices=["sweep", "batch", "recon", "learned", "buried"],
+    ap.add_argument("--workload", default="sweep", choices=["sweep", "batch", "recon", "learned", "buried", "convergence"],
                     help="sweep: the headline 512x512x1024 9-angle step; batch: 64 uneven "
                          "structures in one graph; recon: time to a fixed chi^2; learned: "
-                         "learned vs zero vs constant start")
+                         "learned vs zero vs constant start; buried: coarse Si/Au voxels under the "
+                         "surface; convergence: intensity error vs slice thickness")
     ap.add_argument("--train-samples", type=int, default=100000)
     ap.add_argument("--heldout", type=int, default=10)
     ap.add_argument("--chunk", type=int, default=64, help="learned: structures per forward launch")
@@ -798,6 +854,8 @@ def main():
         return run_learned(args)
     if args.workload == "buried":
         return run_buried(args)
+    if args.workload == "convergence":
+        return run_convergence(args)
     return run_gpu(args)
 
 

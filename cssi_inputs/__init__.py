@@ -165,3 +165,40 @@ def batched_jobs(seed, njobs=64):
 def sweep_angles_deg(n=9, lo=0.1, hi=0.5):
     """Incidence angles swept across the Si critical angle (~0.22 deg)."""
     return np.linspace(lo, hi, n)
+
+
+def boxes_nm(seed, ny, nz, length_nm, dz_nm=2.0, count=20):
+    """Au boxes standing on the Si surface, with their extent along the beam in
+    nm rather than in slices, so that one structure can be sliced at any
+    thickness.  Returns rows (x0_nm, x1_nm, y0, y1, height_rows): x-length
+    uniform in [2, 32] % of length_nm, y-width in [2, ny/8] pixels, height
+    5-60 nm; footprints do not overlap."""
+    rng = np.random.default_rng(seed)
+    h = (max(1, int(round(5.0 / dz_nm))), int(round(60.0 / dz_nm)))
+    boxes = []
+    for _ in range(count):
+        for _try in range(200):
+            lx = float(rng.uniform(0.02, 0.32)) * length_nm
+            x0 = float(rng.uniform(0.0, length_nm - lx))
+            wy = int(rng.integers(2, max(3, ny // 8) + 1))
+            y0 = int(rng.integers(0, ny - wy + 1))
+            ok = all(x0 >= b[1] or x0 + lx <= b[0] or y0 >= b[3] or y0 + wy <= b[2] for b in boxes)
+            if ok:
+                boxes.append((x0, x0 + lx, y0, y0 + wy, min(int(rng.integers(h[0], h[1] + 1)), nz - nz // 2)))
+                break
+    return boxes
+
+
+def slice_boxes(boxes, ny, nz, length_nm, slice_nm, dtype=np.complex64):
+    """Si substrate plus the boxes of `boxes_nm`, cut into round(length/slice)
+    slices of thickness slice_nm.  A slice's voxel is the box's occupancy
+    averaged over the slice's thickness (the fraction of [j D, (j+1) D] that
+    the box covers), times the Au index."""
+    ns = int(round(length_nm / slice_nm))
+    vol = substrate(ny, nz, ns, dtype=np.complex128)
+    surf = nz // 2
+    edges = np.arange(ns + 1) * slice_nm
+    for x0, x1, y0, y1, hgt in boxes:
+        frac = np.clip(np.minimum(edges[1:], x1) - np.maximum(edges[:-1], x0), 0.0, None) / slice_nm
+        vol[:, surf:surf + hgt, y0:y1] += frac[:, None, None] * AU
+    return vol.astype(dtype)

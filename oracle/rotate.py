@@ -93,3 +93,22 @@ def rotate_adjoint(g, spacing, alpha_rad, psi_rad, center_nm):
     for ix, iz, iy, w in _weights(g.shape, spacing, alpha_rad, psi_rad, center_nm):
         np.add.at(out, (ix, iz, iy), w * g)
     return out
+
+
+def rotate_at(vol, spacing, alpha_rad, psi_rad, center_nm, idx):
+    """`rotate` evaluated only at the lab voxels idx[k] = (j, l, m), for volumes
+    too large to resample whole on the host."""
+    idx = np.asarray(idx, dtype=np.int64).reshape(-1, 3)
+    sp = np.asarray(spacing, dtype=np.float64)
+    c = np.asarray(center_nm, dtype=np.float64)
+    f = (c + (idx * sp - c) @ rotation(alpha_rad, psi_rad)) / sp
+    axes = [_stencil(f[:, a], vol.shape[a]) for a in range(3)]
+    out = np.zeros(len(idx), np.complex128)
+    for bx in (0, 1):
+        for bz in (0, 1):
+            for by in (0, 1):
+                w = ((axes[0][1] if bx else 1 - axes[0][1]) * (axes[1][1] if bz else 1 - axes[1][1])
+                     * (axes[2][1] if by else 1 - axes[2][1]))
+                out += w * vol[axes[0][2] if bx else axes[0][0], axes[1][2] if bz else axes[1][0],
+                               axes[2][2] if by else axes[2][0]].astype(np.complex128)
+    return out

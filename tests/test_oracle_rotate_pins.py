@@ -98,3 +98,55 @@ def test_adjoint_is_the_transpose(shape, alpha_deg, psi_deg):
     lhs = np.vdot(R.rotate(v, SP, a, p, c), u)
     rhs = np.vdot(v, R.rotate_adjoint(u, SP, a, p, c))
     assert abs(lhs - rhs) < 1e-12 * abs(lhs)
+
+
+def _equivalence_case():
+    """Si substrate with four Au boxes and absorbing beta ramps in the top and
+    bottom 24 rows; alpha chosen so that k sin(alpha) is m = 17 detector bins."""
+    import cssi_inputs as ci
+    ny, nz, ns, dz, delta, m = 32, 256, 256, 2.0, 20.0, 17
+    alpha = np.arcsin(m * ci.WAVELENGTH_NM / (nz * dz))
+    vol = ci.substrate(ny, nz, ns).astype(np.complex128)
+    rng = np.random.default_rng(0)
+    for _ in range(4):
+        x0, lx = rng.integers(0, ns - 60), rng.integers(20, 60)
+        y0, h = rng.integers(0, ny - 8), rng.integers(5, 20)
+        vol[x0:x0 + lx, nz // 2:nz // 2 + h, y0:y0 + 8] = ci.AU
+    ramp = np.zeros(nz)
+    ramp[:24] = np.linspace(1, 0, 24) ** 2
+    ramp[-24:] = np.linspace(0, 1, 24) ** 2
+    vol += 2e-5j * ramp[None, :, None]
+    return vol, (ny, nz, ns, dz, delta, m, alpha)
+
+
+def test_lab_frame_equals_sample_frame_with_a_tilted_probe(oracle_lib):
+    """The paper's lab frame (volume rotated by Eq. 2-3, straight beam) and the
+    sample frame of the slice loops (probe tilted by alpha) are related by a
+    Galilean boost of the paraxial equation: their far fields agree after a
+    shift of k sin(alpha) along k_z.  The frames coincide at the entrance
+    face (rotation centre x = 0 on the surface)."""
+    vol, (ny, nz, ns, dz, delta, m, alpha) = _equivalence_case()
+    geo_s = oracle_lib.Geometry(ny, nz, ns, slice_nm=delta, dz_nm=dz, alpha_i_deg=(np.rad2deg(alpha),))
+    I_s = oracle_lib.forward(geo_s, vol)[0]
+    c = (0.0, (nz / 2 - 0.5) * dz, (ny - 1) / 2 * 2.0)
+    geo_l = oracle_lib.Geometry(ny, nz, ns, slice_nm=delta, dz_nm=dz, alpha_i_deg=(0.0,))
+    I_l = oracle_lib.forward(geo_l, R.rotate(vol, (delta, dz, 2.0), alpha, 0.0, c))[0]
+    shifted = np.roll(I_s, m, axis=0)
+    err = np.linalg.norm(I_l - shifted) / np.linalg.norm(I_l)
+    assert err < 5e-3
+    # the opposite pitch (surface falling away from the beam) is far off
+    I_bad = oracle_lib.forward(geo_l, R.rotate(vol, (delta, dz, 2.0), -alpha, 0.0, c))[0]
+    assert np.linalg.norm(I_bad - shifted) / np.linalg.norm(I_bad) > 5 * err
+    # and without the shift the two frames disagree entirely
+    assert np.linalg.norm(I_l - I_s) / np.linalg.norm(I_l) > 0.5
+
+
+def test_pointwise_evaluation_matches_the_whole_volume():
+    rng = np.random.default_rng(4)
+    shape = (9, 12, 10)
+    v = rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+    args = (SP, np.deg2rad(1.7), np.deg2rad(-2.2), (60.0, 9.0, 8.0))
+    full = R.rotate(v, *args)
+    idx = np.stack([rng.integers(0, n, 50) for n in shape], axis=1)
+    np.testing.assert_allclose(R.rotate_at(v, *args, idx), full[idx[:, 0], idx[:, 1], idx[:, 2]], rtol=0,
+                               atol=1e-14)

@@ -810,6 +810,53 @@ def run_convergence(args):
     return 0
 
 
+def run_rotate(args):
+    """Frame rotation of Eq. 2-3 on the headline volume (512x512x1024, Si + 50
+    Au pillars/lines): lab-frame resampling at 0.3 deg pitch and 0.5 deg yaw,
+    and its transpose; HBM bandwidth against the measured copy rate (8 B read
+    and 8 B written per voxel)."""
+    import torch
+
+    import cssi_inputs as ci
+    from paper_2212_01253_gb300 import binding as B
+    from paper_2212_01253_gb300 import build as cuda_build
+
+    cuda_build.build()
+    torch.cuda.set_device(0)
+    ns, nz, ny = NS, NZ, NY
+    p = B.make_params(ny, nz, ns, (0.3,), LAM, SLICE, DY, DZ)
+    vol = torch.from_numpy(ci.pillars_large(0)).cuda()
+    out = torch.empty_like(vol)
+    c = (0.0, (nz / 2 - 0.5) * DZ, (ny - 1) / 2 * DY)
+    a, ps = np.deg2rad(0.3), np.deg2rad(0.5)
+    peak = float(measured_peaks().get("hbm_gbs", 6800.0))
+    res = {}
+    for name, fn, src in (("rotate", B.mslice_rotate, vol), ("rotate_adjoint", B.mslice_rotate_adjoint, out)):
+        for _ in range(args.warmup):
+            fn(p, a, ps, c, src, out if src is vol else vol)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            fn(p, a, ps, c, src, out if src is vol else vol)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        gbs = vol.numel() * 16 / (ms / 1e3) / 1e9
+        res[name] = {"ms": ms, "voxels_per_s": vol.numel() / (ms / 1e3), "gbs_algorithmic": gbs,
+                     "frac_of_measured_hbm": gbs / peak}
+    line = {"metric": "frame rotation voxels/s", "value": res["rotate"]["voxels_per_s"], "unit": "voxels/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "512x512x1024 volume (Si + 50 Au pillars/lines), pitch 0.3 deg, yaw 0.5 deg, "
+                                   "trilinear; inputs 2 GiB in and out (larger than L2)"},
+            "roofline": {"bound": "hbm", "achieved": res["rotate"]["gbs_algorithmic"], "peak": peak, "unit": "GB/s",
+                         "frac": res["rotate"]["frac_of_measured_hbm"], "traffic": None},
+            "kernels": res}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -822,11 +869,12 @@ def main():
     ap.add_argument("--cpu-angles", type=int, default=3)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="sweep", choices=["sweep", "batch", "recon", "learned", "buried", "convergence"],
+    ap.add_argument("--workload", default="sweep", choices=["sweep", "batch", "recon", "learned", "buried", "convergence", "rotate"],
                     help="sweep: the headline 512x512x1024 9-angle step; batch: 64 uneven "
                          "structures in one graph; recon: time to a fixed chi^2; learned: "
                          "learned vs zero vs constant start; buried: coarse Si/Au voxels under the "
-                         "surface; convergence: intensity error vs slice thickness")
+                         "surface; convergence: intensity error vs slice thickness; rotate: frame "
+                         "rotation of the headline volume")
     ap.add_argument("--train-samples", type=int, default=100000)
     ap.add_argument("--heldout", type=int, default=10)
     ap.add_argument("--chunk", type=int, default=64, help="learned: structures per forward launch")
@@ -856,6 +904,8 @@ def main():
         return run_buried(args)
     if args.workload == "convergence":
         return run_convergence(args)
+    if args.workload == "rotate":
+        return run_rotate(args)
     return run_gpu(args)
 
 

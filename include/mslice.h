@@ -249,12 +249,60 @@ int mslice_fine_to_coarse(const mslice_params *p, const mslice_coarse *c, const 
  * 1 <= nlevels <= 8 levels given in host memory; n parameters, in place. */
 int mslice_snap(float *theta, size_t n, const float *levels, int nlevels, void *stream);
 
+/* Shrink-wrap support update (Sec. 4.2, after Marchesini et al. 2003: every
+ * twenty epochs, also a nearest-neighbour filter between material and air)
+ * on a coarse parameter grid theta[cx][cz][cy], device memory, in place:
+ *   blur    = theta convolved with a normalised Gaussian of width sigma coarse
+ *             voxels, separably along y, then z, then x; taps t = -r..r,
+ *             r = floor(3 sigma + 0.5) <= 16 (else MSLICE_EUNSUPPORTED); zero
+ *             outside the grid;
+ *   support = blur >= threshold * max(blur), 0 <= threshold <= 1;
+ *   theta   = 0 outside the support (air, or the host of a buried pattern).
+ * The blur takes its taps in order with FP32 products and sums rounded one by
+ * one (no fused multiply-add), so the support is reproducible bit for bit.
+ * kept: NULL or a device int that receives the support's size.  ws: device
+ * workspace, 16-byte aligned, of mslice_shrinkwrap_workspace(cx*cz*cy) bytes. */
+size_t mslice_shrinkwrap_workspace(size_t n);
+int mslice_shrinkwrap(float *theta, int cx, int cz, int cy, float sigma, float threshold, int *kept, void *ws,
+                      size_t ws_bytes, void *stream);
+
 /* One ADAM step (Kingma & Ba, cited in Sec. 4.1) on n parameters, in place:
  *   m = b1 m + (1-b1) g;  v = b2 v + (1-b2) g^2;
  *   theta -= lr * (m / (1-b1^t)) / (sqrt(v / (1-b2^t)) + eps);  theta = clamp(theta, lo, hi)
  * t >= 1 is the step number; m and v start at 0. */
 int mslice_adam_step(float *theta, float *m, float *v, const float *grad, size_t n, float lr,
                      float b1, float b2, float eps, int t, float lo, float hi, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Frame rotation (Eq. 2-3): the paper simulates in the lab frame, rotating
+ * the index volume by a pitch of alpha_i after a yaw of psi so that a straight
+ * beam meets it.  The slice loops above work in the sample frame with a
+ * tilted probe instead (the paraxially equivalent form); these calls build
+ * the lab-frame volume for the paper's formulation and map lab-frame
+ * gradients back.
+ *
+ * Axes (x, z, y) with x = j slice_nm, z = l dz_nm, y = m dy_nm; both volumes
+ * are [ns][nz][ny] complex64 on that lattice (ns, nz, ny and the spacings
+ * come from p; its other fields are ignored, and ny, nz need not be powers
+ * of two here).  With M = R_pitch(alpha) R_yaw(psi),
+ *   R_pitch: x' = cos(a) x - sin(a) z,  z' = sin(a) x + cos(a) z
+ *   R_yaw:   x' = cos(p) x - sin(p) y,  y' = sin(p) x + cos(p) y
+ * the lab voxel at r takes the sample volume at s = c + M^T (r - c), c the
+ * rotation centre center_nm[3] = (x, z, y) in host memory: the surface rises
+ * by tan(alpha) along +x and a feature drifts toward +y by tan(psi).
+ * Trilinear interpolation in index units, each index clamped to [0, n-1]
+ * (the volume extends past its faces by its edge values).
+ * ------------------------------------------------------------------------ */
+
+/* vol_lab = R vol_sample.  Device buffers, no aliasing; asynchronous on stream. */
+int mslice_rotate(const mslice_params *p, double alpha_rad, double psi_rad, const double *center_nm,
+                  const float *vol_sample, float *vol_lab, void *stream);
+
+/* g_sample = R^T g_lab (overwritten): the lab-frame gradient scattered back
+ * with the interpolation weights.  Summed with float atomics, so the result
+ * is not bitwise reproducible from run to run. */
+int mslice_rotate_adjoint(const mslice_params *p, double alpha_rad, double psi_rad, const double *center_nm,
+                          const float *g_lab, float *g_sample, void *stream);
 
 /* ------------------------------------------------------------------------
  * Learned initialiser kernels: a small network maps the log-scaled detector

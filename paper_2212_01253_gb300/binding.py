@@ -136,6 +136,13 @@ def _load():
                 "mslice_coarse_to_fine": ([P, ctypes.POINTER(mslice_coarse), vp, vp, vp], ctypes.c_int),
                 "mslice_fine_to_coarse": ([P, ctypes.POINTER(mslice_coarse), vp, vp, vp], ctypes.c_int),
                 "mslice_snap": ([vp, sz, ctypes.POINTER(ctypes.c_float), ctypes.c_int, vp], ctypes.c_int),
+                "mslice_shrinkwrap_workspace": ([sz], sz),
+                "mslice_shrinkwrap": ([vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_float, ctypes.c_float,
+                                       vp, vp, sz, vp], ctypes.c_int),
+                "mslice_rotate": ([P, ctypes.c_double, ctypes.c_double, ctypes.POINTER(ctypes.c_double), vp, vp,
+                                   vp], ctypes.c_int),
+                "mslice_rotate_adjoint": ([P, ctypes.c_double, ctypes.c_double, ctypes.POINTER(ctypes.c_double),
+                                           vp, vp, vp], ctypes.c_int),
                 "mslice_adam_step": ([vp, vp, vp, vp, sz, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                                       ctypes.c_float, ctypes.c_int, ctypes.c_float, ctypes.c_float, vp],
                                      ctypes.c_int),
@@ -417,6 +424,41 @@ def mslice_nn_rasterize_boxes(boxes, out, shape, value, stream=None):
     _check(_load().mslice_nn_rasterize_boxes(
         _ptr(boxes, torch.int32, ns_ * nb_ * 6, "boxes"), nb_, ns_, d0, d1, d2, float(value),
         _ptr(out, torch.float32, ns_ * d0 * d1 * d2, "out"), _stream(stream)), "mslice_nn_rasterize_boxes")
+
+
+def mslice_rotate(p, alpha_rad, psi_rad, center_nm, vol_sample, vol_lab, stream=None):
+    """vol_lab = R vol_sample: the sample-frame volume rotated into the lab frame
+    (pitch alpha after yaw psi about center_nm = (x, z, y) in nm)."""
+    n = p.ns * p.nz * p.ny
+    c = (ctypes.c_double * 3)(*[float(v) for v in center_nm])
+    _check(_load().mslice_rotate(ctypes.byref(p), float(alpha_rad), float(psi_rad), c,
+                                 _ptr(vol_sample, torch.complex64, n, "vol_sample"),
+                                 _ptr(vol_lab, torch.complex64, n, "vol_lab"), _stream(stream)), "mslice_rotate")
+
+
+def mslice_rotate_adjoint(p, alpha_rad, psi_rad, center_nm, g_lab, g_sample, stream=None):
+    """g_sample = R^T g_lab (overwritten)."""
+    n = p.ns * p.nz * p.ny
+    c = (ctypes.c_double * 3)(*[float(v) for v in center_nm])
+    _check(_load().mslice_rotate_adjoint(ctypes.byref(p), float(alpha_rad), float(psi_rad), c,
+                                         _ptr(g_lab, torch.complex64, n, "g_lab"),
+                                         _ptr(g_sample, torch.complex64, n, "g_sample"), _stream(stream)),
+           "mslice_rotate_adjoint")
+
+
+def mslice_shrinkwrap(theta, sigma, threshold, kept=None, ws=None, stream=None):
+    """In place on theta [cx][cz][cy] (float32, CUDA): zero outside the
+    shrink-wrap support (Gaussian blur of width sigma, threshold * its max)."""
+    if theta.dim() != 3:
+        raise ValueError("theta must be [cx][cz][cy]")
+    cx, cz, cy = theta.shape
+    need = _load().mslice_shrinkwrap_workspace(theta.numel())
+    if ws is None:
+        ws = torch.empty(need, dtype=torch.uint8, device=theta.device)
+    _check(_load().mslice_shrinkwrap(_ptr(theta, torch.float32, None, "theta"), cx, cz, cy, float(sigma),
+                                     float(threshold), _ptr(kept, torch.int32, 1, "kept"),
+                                     _ptr(ws, torch.uint8, None, "ws"), ws.numel(), _stream(stream)),
+           "mslice_shrinkwrap")
 
 
 def mslice_snap(theta, levels, stream=None):

@@ -47,7 +47,8 @@ def _units():
     inc = ["-I", os.path.join(ROOT, "include"), "-I", CSRC]
     units = [(os.path.join(CSRC, "mslice.cu"), os.path.join(BUILD_DIR, "mslice.o"), inc),
              (os.path.join(CSRC, "mslice_recon.cu"), os.path.join(BUILD_DIR, "mslice_recon.o"), inc),
-             (os.path.join(CSRC, "mslice_nn.cu"), os.path.join(BUILD_DIR, "mslice_nn.o"), inc)]
+             (os.path.join(CSRC, "mslice_nn.cu"), os.path.join(BUILD_DIR, "mslice_nn.o"), inc),
+             (os.path.join(CSRC, "mslice_rotate.cu"), os.path.join(BUILD_DIR, "mslice_rotate.o"), inc)]
     for ny in ROW_LENGTHS:
         units.append((os.path.join(CSRC, "mslice_inst.cu"), os.path.join(BUILD_DIR, "inst_ny%d.o" % ny),
                       inc + ["-DMS_NY=%d" % ny]))

@@ -592,7 +592,9 @@ def run_buried(args):
         meas, sc = ci.poisson_target(I_gt, COUNTS, seed=seed)
         chi2_gt = 4 * ((np.sqrt(sc * I_gt) - meas) ** 2).sum() / meas.size
         R = Reconstructor(p, c, base, torch.from_numpy(meas).cuda(), sc, lr=args.lr, lo=0.0, hi=d_au,
-                          snap_every=args.snap_every, snap_levels=(0.0, d_au), snap_start=args.snap_start)
+                          snap_every=args.snap_every, snap_levels=(0.0, d_au), snap_start=args.snap_start,
+                          shrinkwrap_every=args.shrinkwrap_every, shrinkwrap_sigma=args.shrinkwrap_sigma,
+                          shrinkwrap_threshold=args.shrinkwrap_threshold)
         it, sec, hist = R.run(chi2_target=1.1 * chi2_gt, max_iters=args.max_iters, check_every=20)
         th = R.theta.cpu().numpy().reshape(shape)
         rows.append({"seed": seed, "reached": bool(hist and hist[-1][1] <= 1.1 * chi2_gt), "epochs": it,
@@ -607,9 +609,11 @@ def run_buried(args):
             "config": {"workload": "256x256 grid (2 nm), 512 slices of 20 nm, 0.5 deg; 6x6x6 coarse voxels "
                                    "(1.6 um x 16 nm x 80 nm) of Si or Au buried 10 nm under the Si surface, "
                                    "35 %% Au%s; Poisson target 1e6 counts; start pure Si; ADAM lr %g, snapping "
-                                   "to {Si, Au} every %d epochs from epoch %d; cap %d epochs"
+                                   "to {Si, Au} every %d epochs from epoch %d; shrink-wrap every %d epochs "
+                                   "(sigma %g, threshold %g); cap %d epochs"
                                    % (", uniform along the beam" if args.buried_extrude else "", args.lr,
-                                      args.snap_every, args.snap_start, args.max_iters)}}
+                                      args.snap_every, args.snap_start, args.shrinkwrap_every,
+                                      args.shrinkwrap_sigma, args.shrinkwrap_threshold, args.max_iters)}}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -881,6 +885,9 @@ def main():
     ap.add_argument("--snap-every", type=int, default=20, help="buried: material snapping period (epochs)")
     ap.add_argument("--snap-start", type=int, default=0, help="buried: first epoch that snaps")
     ap.add_argument("--buried-extrude", action="store_true", help="buried: pattern uniform along the beam")
+    ap.add_argument("--shrinkwrap-every", type=int, default=0, help="buried: shrink-wrap support period (0: off)")
+    ap.add_argument("--shrinkwrap-sigma", type=float, default=1.0, help="buried: shrink-wrap blur (coarse voxels)")
+    ap.add_argument("--shrinkwrap-threshold", type=float, default=0.2, help="buried: shrink-wrap threshold")
     ap.add_argument("--recon-angles", type=int, default=1, help="recon: incidence angles (views) sharing the volume")
     ap.add_argument("--checkpoint", type=int, default=0,
                     help="adjoint checkpoint interval (0: keep every a_j when it fits in half the HBM, else 32)")

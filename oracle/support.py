@@ -24,11 +24,15 @@ import numpy as np
 
 
 def taps(sigma):
-    """Normalised Gaussian weights for t = -r..r (double)."""
-    r = int(np.floor(3.0 * sigma + 0.5))
-    t = np.arange(-r, r + 1, dtype=np.float64)
-    w = np.exp(-t * t / (2.0 * sigma * sigma))
-    return w / w.sum()
+    """Normalised Gaussian weights for t = -r..r (double): libm exp and a sum
+    in tap order, so that the FP32 weights come out as the library's do."""
+    import math
+    r = int(math.floor(3.0 * sigma + 0.5))
+    w = [math.exp(-float(t * t) / (2.0 * sigma * sigma)) for t in range(-r, r + 1)]
+    total = 0.0
+    for x in w:
+        total += x
+    return np.array([x / total for x in w])
 
 
 def _shift(a, t, axis):

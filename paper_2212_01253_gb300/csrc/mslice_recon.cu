@@ -93,6 +93,62 @@ __global__ void k_snap(float* __restrict__ th, size_t n, SnapLevels L) {
     }
 }
 
+// shrink-wrap support update (Sec. 4.2): separable Gaussian blur, maximum,
+// threshold.  Products and sums are rounded one by one (no fused
+// multiply-add) and taken in tap order, so the support decision is
+// reproducible.
+constexpr int kMaxTapRadius = 16;
+struct Taps {
+    float w[2 * kMaxTapRadius + 1];
+    int r;
+};
+
+__global__ void k_blur_axis(const float* __restrict__ in, float* __restrict__ out, int cx, int cz, int cy, int axis,
+                            Taps T) {
+    const long n = (long)cx * cz * cy;
+    const long stride = axis == 2 ? 1 : (axis == 1 ? cy : (long)cz * cy);
+    const int len = axis == 2 ? cy : (axis == 1 ? cz : cx);
+    const long gs = (long)gridDim.x * blockDim.x;
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gs) {
+        const int pos = (int)((i / stride) % len);
+        float acc = 0.f;
+        for (int t = -T.r; t <= T.r; ++t) {
+            const int q = pos + t;
+            if (q >= 0 && q < len) acc = __fadd_rn(acc, __fmul_rn(T.w[t + T.r], in[i + (long)t * stride]));
+        }
+        out[i] = acc;
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_max(const float* __restrict__ b, long n, float* __restrict__ mx) {
+    __shared__ float red[32];
+    float m = -INFINITY;
+    for (long i = threadIdx.x; i < n; i += blockDim.x) m = fmaxf(m, b[i]);
+    for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        m = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : -INFINITY;
+        for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (threadIdx.x == 0) *mx = m;
+    }
+}
+
+__global__ void k_support(float* __restrict__ th, const float* __restrict__ b, long n, const float* __restrict__ mx,
+                          float threshold, int* __restrict__ kept) {
+    const float thr = __fmul_rn(threshold, *mx);
+    const long gs = (long)gridDim.x * blockDim.x;
+    int mine = 0;
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gs) {
+        if (b[i] >= thr) ++mine;
+        else th[i] = 0.f;
+    }
+    if (kept) {
+        for (int o = 16; o; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
+        if ((threadIdx.x & 31) == 0 && mine) atomicAdd(kept, mine);
+    }
+}
+
 unsigned blocks_for(size_t n) {
     size_t b = (n + 255) / 256;
     return (unsigned)(b > 4096 ? 4096 : (b ? b : 1));
@@ -127,6 +183,37 @@ int mslice_snap(float* theta, size_t n, const float* levels, int nlevels, void* 
     for (int k = 0; k < nlevels; ++k) L.v[k] = levels[k];
     L.n = nlevels;
     k_snap<<<blocks_for(n), 256, 0, (cudaStream_t)stream>>>(theta, n, L);
+    return cudaGetLastError() == cudaSuccess ? MSLICE_OK : MSLICE_ELAUNCH;
+}
+
+size_t mslice_shrinkwrap_workspace(size_t n) { return (2 * n + 64) * sizeof(float); }
+
+int mslice_shrinkwrap(float* theta, int cx, int cz, int cy, float sigma, float threshold, int* kept, void* ws,
+                      size_t ws_bytes, void* stream) {
+    if (!theta || !ws || cx < 1 || cz < 1 || cy < 1 || !(sigma > 0.f) || !(threshold >= 0.f && threshold <= 1.f))
+        return MSLICE_EINVAL;
+    const size_t n = (size_t)cx * cz * cy;
+    if (ws_bytes < mslice_shrinkwrap_workspace(n) || ((uintptr_t)ws & 15)) return MSLICE_EINVAL;
+    const int r = (int)floor(3.0 * (double)sigma + 0.5);
+    if (r > kMaxTapRadius) return MSLICE_EUNSUPPORTED;
+    Taps T{};
+    T.r = r;
+    double w[2 * kMaxTapRadius + 1], total = 0.0;
+    for (int t = -r; t <= r; ++t) {
+        w[t + r] = exp(-(double)(t * t) / (2.0 * (double)sigma * (double)sigma));
+        total += w[t + r];
+    }
+    for (int k = 0; k <= 2 * r; ++k) T.w[k] = (float)(w[k] / total);
+    cudaStream_t st = (cudaStream_t)stream;
+    float* a = (float*)ws;
+    float* b = a + n;
+    float* mx = b + n;
+    if (kept && cudaMemsetAsync(kept, 0, sizeof(int), st) != cudaSuccess) return MSLICE_ELAUNCH;
+    k_blur_axis<<<blocks_for(n), 256, 0, st>>>(theta, a, cx, cz, cy, 2, T);
+    k_blur_axis<<<blocks_for(n), 256, 0, st>>>(a, b, cx, cz, cy, 1, T);
+    k_blur_axis<<<blocks_for(n), 256, 0, st>>>(b, a, cx, cz, cy, 0, T);
+    k_max<<<1, 1024, 0, st>>>(a, (long)n, mx);
+    k_support<<<blocks_for(n), 256, 0, st>>>(theta, a, (long)n, mx, threshold, kept);
     return cudaGetLastError() == cudaSuccess ? MSLICE_OK : MSLICE_ELAUNCH;
 }
 

@@ -40,13 +40,13 @@ struct RotMap {
 
 // fraction-split index of one axis: lower lattice index and upper weight,
 // clamped to the volume
-__device__ __forceinline__ void axis_stencil(long long ri, float rf, float hi, float lo, int m, int n, int& i0,
-                                             int& i1, float& w) {
+__device__ __forceinline__ void axis_stencil(int ri, float rf, float hi, float lo, int m, int n, int& i0, int& i1,
+                                             float& w) {
     const float t = hi * (float)m;          // exact: 12-bit hi times m < 2^12
     const float ti = floorf(t);
     const float frac = rf + (t - ti) + lo * (float)m;
     const float fi = floorf(frac);
-    const long long i = ri + (long long)ti + (long long)fi;
+    const int i = ri + (int)ti + (int)fi;
     w = frac - fi;
     // past a face: the face value itself, with weight 0 on a neighbour (so
     // that the edge value passes through exactly)
@@ -57,70 +57,105 @@ __device__ __forceinline__ void axis_stencil(long long ri, float rf, float hi, f
         i0 = n - 1;
         w = 0.f;
     } else {
-        i0 = (int)i;
+        i0 = i;
     }
     i1 = i0 + 1 < n ? i0 + 1 : n - 1;
 }
 
-__device__ __forceinline__ void row_split(const RotMap& R, int j, int l, long long (&ri)[3], float (&rf)[3]) {
+struct Stencil {
+    size_t a00, a01, a10, a11;   // sample rows (x0,z0) (x0,z1) (x1,z0) (x1,z1)
+    int y0, y1;
+    float w000, w001, w100, w101, wy;
+};
+
+__device__ __forceinline__ Stencil stencil(const RotMap& R, const int (&ri)[3], const float (&rf)[3], int m) {
+    int x0, x1, z0, z1;
+    float wx, wz;
+    Stencil S;
+    axis_stencil(ri[0], rf[0], R.hi[0], R.lo[0], m, R.n[0], x0, x1, wx);
+    axis_stencil(ri[1], rf[1], R.hi[1], R.lo[1], m, R.n[1], z0, z1, wz);
+    axis_stencil(ri[2], rf[2], R.hi[2], R.lo[2], m, R.n[2], S.y0, S.y1, S.wy);
+    const size_t plane = (size_t)R.n[1] * R.n[2];
+    S.a00 = (size_t)x0 * plane + (size_t)z0 * R.n[2];
+    S.a01 = (size_t)x0 * plane + (size_t)z1 * R.n[2];
+    S.a10 = (size_t)x1 * plane + (size_t)z0 * R.n[2];
+    S.a11 = (size_t)x1 * plane + (size_t)z1 * R.n[2];
+    S.w000 = (1.f - wx) * (1.f - wz);
+    S.w001 = (1.f - wx) * wz;
+    S.w100 = wx * (1.f - wz);
+    S.w101 = wx * wz;
+    return S;
+}
+
+__device__ __forceinline__ float2 lerp_y(const float2* __restrict__ in, size_t a, const Stencil& S) {
+    const float2 v0 = __ldg(in + a + S.y0), v1 = __ldg(in + a + S.y1);
+    return make_float2(fmaf(S.wy, v1.x - v0.x, v0.x), fmaf(S.wy, v1.y - v0.y, v0.y));
+}
+
+__device__ __forceinline__ float2 gather(const float2* __restrict__ in, const Stencil& S) {
+    const float2 p00 = lerp_y(in, S.a00, S), p01 = lerp_y(in, S.a01, S);
+    const float2 p10 = lerp_y(in, S.a10, S), p11 = lerp_y(in, S.a11, S);
+    return make_float2(S.w000 * p00.x + S.w001 * p01.x + S.w100 * p10.x + S.w101 * p11.x,
+                       S.w000 * p00.y + S.w001 * p01.y + S.w100 * p10.y + S.w101 * p11.y);
+}
+
+__device__ __forceinline__ void scatter(float2* __restrict__ out, const Stencil& S, float2 g) {
+    float* dst = reinterpret_cast<float*>(out);
+    const size_t base[4] = {S.a00, S.a01, S.a10, S.a11};
+    const float wb[4] = {S.w000, S.w001, S.w100, S.w101};
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        const double f = fma(R.A[k][1], (double)l, fma(R.A[k][0], (double)j, R.b[k]));
-        const double fl = floor(f);
-        ri[k] = (long long)fl;
-        rf[k] = (float)(f - fl);
+    for (int q = 0; q < 4; ++q) {
+        const float w0 = wb[q] * (1.f - S.wy), w1 = wb[q] * S.wy;
+        atomicAdd(dst + 2 * (base[q] + S.y0), w0 * g.x);
+        atomicAdd(dst + 2 * (base[q] + S.y0) + 1, w0 * g.y);
+        atomicAdd(dst + 2 * (base[q] + S.y1), w1 * g.x);
+        atomicAdd(dst + 2 * (base[q] + S.y1) + 1, w1 * g.y);
     }
 }
 
-// one warp per lab row (j, l), lanes along y
+// one warp per lab row (j, l), lanes along y, two voxels per lane and step
+// (their loads in flight together).  Lanes 0..2 form the row's FP64 index
+// terms, one axis each, and pass them to the warp.
 template <bool ADJ>
 __global__ void __launch_bounds__(256) k_rotate(const float2* __restrict__ in, float2* __restrict__ out,
                                                 const RotMap R) {
     const int lane = threadIdx.x & 31;
-    const long long rows = (long long)R.n[0] * R.n[1];
-    const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
-    const size_t plane = (size_t)R.n[1] * R.n[2];
-    for (long long row = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); row < rows;
-         row += warps) {
-        const int j = (int)(row / R.n[1]), l = (int)(row % R.n[1]);
-        long long ri[3];
+    const unsigned rows = (unsigned)R.n[0] * (unsigned)R.n[1];
+    const unsigned warps = gridDim.x * (blockDim.x >> 5);
+    const int ny = R.n[2];
+    for (unsigned row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); row < rows; row += warps) {
+        const unsigned j = row / (unsigned)R.n[1], l = row - j * (unsigned)R.n[1];
+        int ri_k = 0;
+        float rf_k = 0.f;
+        if (lane < 3) {
+            const double b = lane == 0 ? R.b[0] : (lane == 1 ? R.b[1] : R.b[2]);
+            const double aj = lane == 0 ? R.A[0][0] : (lane == 1 ? R.A[1][0] : R.A[2][0]);
+            const double al = lane == 0 ? R.A[0][1] : (lane == 1 ? R.A[1][1] : R.A[2][1]);
+            const double f = fma(al, (double)l, fma(aj, (double)j, b));
+            const double fl = floor(f);
+            ri_k = (int)fl;
+            rf_k = (float)(f - fl);
+        }
+        int ri[3];
         float rf[3];
-        row_split(R, j, l, ri, rf);
-        for (int m = lane; m < R.n[2]; m += 32) {
-            int x0, x1, z0, z1, y0, y1;
-            float wx, wz, wy;
-            axis_stencil(ri[0], rf[0], R.hi[0], R.lo[0], m, R.n[0], x0, x1, wx);
-            axis_stencil(ri[1], rf[1], R.hi[1], R.lo[1], m, R.n[1], z0, z1, wz);
-            axis_stencil(ri[2], rf[2], R.hi[2], R.lo[2], m, R.n[2], y0, y1, wy);
-            const size_t a00 = (size_t)x0 * plane + (size_t)z0 * R.n[2], a01 = (size_t)x0 * plane + (size_t)z1 * R.n[2];
-            const size_t a10 = (size_t)x1 * plane + (size_t)z0 * R.n[2], a11 = (size_t)x1 * plane + (size_t)z1 * R.n[2];
-            const float w000 = (1.f - wx) * (1.f - wz), w001 = (1.f - wx) * wz;
-            const float w100 = wx * (1.f - wz), w101 = wx * wz;
-            const size_t o = (size_t)row * R.n[2] + m;
-            if constexpr (!ADJ) {
-                const float2 v000 = __ldg(in + a00 + y0), v001 = __ldg(in + a00 + y1);
-                const float2 v010 = __ldg(in + a01 + y0), v011 = __ldg(in + a01 + y1);
-                const float2 v100 = __ldg(in + a10 + y0), v101 = __ldg(in + a10 + y1);
-                const float2 v110 = __ldg(in + a11 + y0), v111 = __ldg(in + a11 + y1);
-                const float2 p00 = make_float2(fmaf(wy, v001.x - v000.x, v000.x), fmaf(wy, v001.y - v000.y, v000.y));
-                const float2 p01 = make_float2(fmaf(wy, v011.x - v010.x, v010.x), fmaf(wy, v011.y - v010.y, v010.y));
-                const float2 p10 = make_float2(fmaf(wy, v101.x - v100.x, v100.x), fmaf(wy, v101.y - v100.y, v100.y));
-                const float2 p11 = make_float2(fmaf(wy, v111.x - v110.x, v110.x), fmaf(wy, v111.y - v110.y, v110.y));
-                out[o] = make_float2(w000 * p00.x + w001 * p01.x + w100 * p10.x + w101 * p11.x,
-                                     w000 * p00.y + w001 * p01.y + w100 * p10.y + w101 * p11.y);
-            } else {
-                const float2 g = __ldg(in + o);
-                float* dst = reinterpret_cast<float*>(out);
-                const size_t base[4] = {a00, a01, a10, a11};
-                const float wb[4] = {w000, w001, w100, w101};
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const float w0 = wb[q] * (1.f - wy), w1 = wb[q] * wy;
-                    atomicAdd(dst + 2 * (base[q] + y0), w0 * g.x);
-                    atomicAdd(dst + 2 * (base[q] + y0) + 1, w0 * g.y);
-                    atomicAdd(dst + 2 * (base[q] + y1), w1 * g.x);
-                    atomicAdd(dst + 2 * (base[q] + y1) + 1, w1 * g.y);
-                }
+        for (int k = 0; k < 3; ++k) {
+            ri[k] = __shfl_sync(0xffffffffu, ri_k, k);
+            rf[k] = __shfl_sync(0xffffffffu, rf_k, k);
+        }
+        const size_t o = (size_t)row * ny;
+        for (int m = lane; m < ny; m += 64) {
+            const bool two = m + 32 < ny;
+            const Stencil S0 = stencil(R, ri, rf, m);
+            const Stencil S1 = stencil(R, ri, rf, two ? m + 32 : m);
+            if constexpr (!ADJ) {
+                const float2 v0 = gather(in, S0);
+                const float2 v1 = gather(in, S1);
+                out[o + m] = v0;
+                if (two) out[o + m + 32] = v1;
+            } else {
+                scatter(out, S0, __ldg(in + o + m));
+                if (two) scatter(out, S1, __ldg(in + o + m + 32));
             }
         }
     }
@@ -163,6 +198,17 @@ int make_map(const mslice_params* p, double alpha, double psi, const double* c, 
     R->n[0] = p->ns;
     R->n[1] = p->nz;
     R->n[2] = p->ny;
+    // the kernel keeps rows and lattice indices in 32 bits: the map is affine,
+    // so its extremes over the volume are at the corners
+    if ((double)p->ns * p->nz >= 2147483648.0) return MSLICE_EUNSUPPORTED;
+    for (int k = 0; k < 3; ++k)
+        for (int cj = 0; cj < 2; ++cj)
+            for (int cl = 0; cl < 2; ++cl)
+                for (int cm = 0; cm < 2; ++cm) {
+                    const double f = R->b[k] + R->A[k][0] * (cj ? p->ns - 1 : 0) + R->A[k][1] * (cl ? p->nz - 1 : 0) +
+                                     ((double)R->hi[k] + R->lo[k]) * (cm ? p->ny - 1 : 0);
+                    if (!(fabs(f) < 1073741824.0)) return MSLICE_EUNSUPPORTED;
+                }
     return MSLICE_OK;
 }
 
@@ -175,7 +221,7 @@ int launch(const mslice_params* p, double alpha, double psi, const double* c, co
     cudaStream_t st = (cudaStream_t)stream;
     const size_t n = (size_t)p->ns * p->nz * p->ny;
     const long long rows = (long long)p->ns * p->nz;
-    const unsigned blocks = (unsigned)(rows / 8 + 1 < 152 * 16 ? rows / 8 + 1 : 152 * 16);
+    const unsigned blocks = (unsigned)(rows / 8 + 1 < 152 * 32 ? rows / 8 + 1 : 152 * 32);
     if (adjoint) {
         if (cudaMemsetAsync(out, 0, n * sizeof(float2), st) != cudaSuccess) return MSLICE_ELAUNCH;
         k_rotate<true><<<blocks, 256, 0, st>>>((const float2*)in, (float2*)out, R);

@@ -3,6 +3,7 @@
 loss of Eq. 4, ADAM).  Every step runs in libmslice kernels:
 
     E (coarse -> fine) -> mslice_loss_grad -> E^T -> ADAM (clamped to [lo, hi])
+    [-> shrink-wrap support every shrinkwrap_every iterations]
     [-> material snapping every snap_every iterations]
 
 The fine volume keeps its fixed part (substrate, vacuum) outside the coarse
@@ -20,7 +21,8 @@ from . import binding as B
 
 class Reconstructor:
     def __init__(self, params, coarse, base_vol, meas_amp, scale, theta0=None, lr=2e-6, lo=0.0, hi=4.7e-5,
-                 b1=0.9, b2=0.999, eps=1e-20, probe=None, snap_every=0, snap_levels=None, snap_start=0):
+                 b1=0.9, b2=0.999, eps=1e-20, probe=None, snap_every=0, snap_levels=None, snap_start=0,
+                 shrinkwrap_every=0, shrinkwrap_sigma=1.0, shrinkwrap_threshold=0.2):
         dev = base_vol.device
         self.p, self.c = params, coarse
         self.vol = base_vol.clone()
@@ -44,6 +46,12 @@ class Reconstructor:
         self.snap_every = int(snap_every)
         self.snap_levels = list(snap_levels) if snap_levels is not None else None
         self.snap_start = int(snap_start)
+        # shrink-wrap support (Sec. 4.2): every shrinkwrap_every iterations the
+        # coarse voxels outside the thresholded Gaussian blur of theta go to 0
+        self.sw_every = int(shrinkwrap_every)
+        self.sw_sigma, self.sw_threshold = float(shrinkwrap_sigma), float(shrinkwrap_threshold)
+        self.sw_ws = (torch.empty(B._load().mslice_shrinkwrap_workspace(n), dtype=torch.uint8, device=dev)
+                      if self.sw_every else None)
 
     def step(self):
         """One iteration; returns nothing (the loss of the current theta lands in self.loss)."""
@@ -54,6 +62,9 @@ class Reconstructor:
         B.mslice_fine_to_coarse(self.p, self.c, self.grad, self.g_theta)
         B.mslice_adam_step(self.theta, self.m, self.v, self.g_theta, self.lr, self.b1, self.b2, self.eps,
                            self.t, self.lo, self.hi)
+        if self.sw_every and self.t % self.sw_every == 0:
+            B.mslice_shrinkwrap(self.theta.view(self.c.cx, self.c.cz, self.c.cy), self.sw_sigma, self.sw_threshold,
+                                ws=self.sw_ws)
         if self.snap_every and self.snap_levels and self.t >= self.snap_start and self.t % self.snap_every == 0:
             B.mslice_snap(self.theta, self.snap_levels)
 

@@ -67,6 +67,7 @@ class OrcParams(ctypes.Structure):
         ("exact", ctypes.c_int32),
         ("psi_rad", ctypes.c_double),
         ("strang", ctypes.c_int32),
+        ("angular", ctypes.c_int32),
     ]
 
 
@@ -98,11 +99,15 @@ class Geometry:
     """Grid and beam: lambda, Delta, dy, dz, (Ny, Nz, Ns) and the incidence angles."""
 
     def __init__(self, ny, nz, ns, wavelength_nm=0.155, slice_nm=20.0, dy_nm=2.0,
-                 dz_nm=2.0, alpha_i_deg=(0.3,), exact_transmission=False, psi_deg=0.0, strang=False):
+                 dz_nm=2.0, alpha_i_deg=(0.3,), exact_transmission=False, psi_deg=0.0, strang=False,
+                 angular=False):
         self.ny, self.nz, self.ns = int(ny), int(nz), int(ns)
         # symmetric splitting: half a step of propagation before the first
         # slice (and after the last, for the exit wave)
         self.strang = bool(strang)
+        # angular-spectrum propagator exp(i Delta (sqrt(k^2 - k_perp^2) - k))
+        # instead of the paraxial Fresnel one
+        self.angular = bool(angular)
         # exact 1 - n^2 in the transmission of Eq. 1 instead of 2 (delta - i beta)
         self.exact_transmission = bool(exact_transmission)
         self.psi_rad = float(np.deg2rad(psi_deg))      # in-plane angle of the default probe
@@ -121,7 +126,7 @@ class Geometry:
                          self.ny, self.nz, self.ns, self.nw,
                          self._alpha_keep.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                          int(bool(naive)), int(bool(exit_wave)), int(self.exact_transmission), self.psi_rad,
-                         int(self.strang))
+                         int(self.strang), int(self.angular))
 
 
 def _c128(a, shape):

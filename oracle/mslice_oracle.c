@@ -29,6 +29,14 @@
  *   I       = |Psi|^2
  *   L       = sum (sqrt(s I) - m)^2   (Eq. 4 on amplitudes, without the 1/N)
  *
+ * With `angular` the propagator is the angular spectrum of the Helmholtz
+ * equation instead of its paraxial (Fresnel) form:
+ *   exp(i Delta (sqrt(k^2 - k_y^2 - k_z^2) - k))
+ *     = exp(-i Delta (k_y^2 + k_z^2) / (sqrt(k^2 - k_y^2 - k_z^2) + k)),
+ * and for k_y^2 + k_z^2 > k^2 (evanescent) exp(-Delta sqrt(k_y^2 + k_z^2 - k^2))
+ * times the carrier phase exp(-i Delta k).  The paraxial form is its
+ * expansion to first order in (k_y^2 + k_z^2) / k^2.
+ *
  * With `strang` the splitting is symmetric instead of transmission-first:
  * half a step of free propagation, then per slice the transmission and a full
  * step, the last step being a half step again:
@@ -84,6 +92,7 @@ typedef struct {
     int32_t exact;            /* 1: exact 1 - n^2 in the transmission instead of 2 (delta - i beta) */
     double psi_rad;           /* in-plane angle: the default probe also carries exp(-i k sin(psi) y) */
     int32_t strang;           /* 1: symmetric splitting (half steps of propagation at both ends) */
+    int32_t angular;          /* 1: angular-spectrum propagator instead of the paraxial one */
 } orc_params;
 
 static int is_pow2(int n) { return n >= 1 && (n & (n - 1)) == 0; }
@@ -196,7 +205,8 @@ static double angular_freq(int m, int n, double d)
 
 /* Fresnel propagator of Eq. 1 on the full 2-D frequency grid over a distance
  * len (Delta, or Delta/2 for the half steps of the symmetric splitting):
- * P[l][m] = exp(-i len (k_y[m]^2 + k_z[l]^2) / (2k)). */
+ * P[l][m] = exp(-i len (k_y[m]^2 + k_z[l]^2) / (2k)); with q->angular the
+ * angular-spectrum propagator written out in the header. */
 static cplx *make_propagator(const orc_params *q, double len)
 {
     const int ny = q->ny, nz = q->nz;
@@ -207,7 +217,13 @@ static cplx *make_propagator(const orc_params *q, double len)
         double kz = angular_freq(l, nz, q->dz_nm);
         for (int m = 0; m < ny; m++) {
             double ky = angular_freq(m, ny, q->dy_nm);
-            P[(size_t)l * ny + m] = cexp(-I * len * (ky * ky + kz * kz) / (2.0 * k));
+            const double kp2 = ky * ky + kz * kz;
+            if (!q->angular)
+                P[(size_t)l * ny + m] = cexp(-I * len * kp2 / (2.0 * k));
+            else if (kp2 < k * k)
+                P[(size_t)l * ny + m] = cexp(-I * len * kp2 / (sqrt(k * k - kp2) + k));
+            else
+                P[(size_t)l * ny + m] = exp(-len * sqrt(kp2 - k * k)) * cexp(-I * len * k);
         }
     }
     return P;

@@ -283,6 +283,51 @@ def test_splitting_order_against_the_matrix_exponential(oracle_lib, strang, orde
     assert errs[-1] < (1e-4 if strang else 2e-2)
 
 
+def _mode(ny, nz, a, b):
+    """The DFT basis vector of bin (k_z index b, k_y index a) on an nz x ny grid."""
+    l, m = np.meshgrid(np.arange(nz), np.arange(ny), indexing="ij")
+    return np.exp(2j * np.pi * (a * m / ny + b * l / nz))
+
+
+def test_angular_spectrum_propagates_a_plane_wave_by_its_exact_phase(oracle_lib):
+    """One Fourier mode through vacuum gains exp(i L (sqrt(k^2 - k_perp^2) - k)),
+    the Helmholtz phase, at a transverse frequency where the paraxial phase
+    is off by 0.15 rad."""
+    ny, nz, ns, d, delta = 16, 32, 40, 0.5, 20.0
+    a, b = 3, -5
+    ky, kz = 2 * np.pi * a / (ny * d), 2 * np.pi * b / (nz * d)
+    kp2 = ky * ky + kz * kz
+    L = ns * delta
+    probe = _mode(ny, nz, a, b)[None]
+    vol = np.zeros((ns, nz, ny), np.complex128)
+    out = {}
+    for angular in (False, True):
+        geo = oracle_lib.Geometry(ny, nz, ns, slice_nm=delta, dy_nm=d, dz_nm=d, alpha_i_deg=(0.0,), angular=angular)
+        out[angular] = oracle_lib.forward(geo, vol, probe=probe, exit_wave=True)[0]
+    exact = probe[0] * np.exp(1j * L * (np.sqrt(K * K - kp2) - K))
+    assert np.abs(out[True] - exact).max() < 1e-10
+    paraxial = probe[0] * np.exp(-1j * L * kp2 / (2 * K))
+    assert np.abs(out[False] - paraxial).max() < 1e-10
+    assert np.abs(exact - paraxial).max() > 0.1
+
+
+def test_angular_spectrum_damps_an_evanescent_mode(oracle_lib):
+    """A mode with k_perp > k decays as exp(-L sqrt(k_perp^2 - k^2)) (times the
+    carrier phase exp(-i L k) of the propagator's convention)."""
+    ny, nz, ns, delta = 16, 4, 4, 0.05
+    a = 7
+    ky = 2 * np.pi * a / (ny * 0.05)
+    assert ky > K
+    probe = _mode(ny, nz, a, 0)[None]
+    geo = oracle_lib.Geometry(ny, nz, ns, slice_nm=delta, dy_nm=0.05, dz_nm=0.05, alpha_i_deg=(0.0,),
+                              angular=True)
+    out = oracle_lib.forward(geo, np.zeros((ns, nz, ny)), probe=probe, exit_wave=True)[0]
+    L = ns * delta
+    exact = probe[0] * np.exp(-L * np.sqrt(ky * ky - K * K)) * np.exp(-1j * L * K)
+    assert np.abs(exact).max() < 1e-2
+    assert np.abs(out - exact).max() < 1e-13
+
+
 def test_symmetric_splitting_in_free_space_is_the_full_propagation(oracle_lib):
     """With delta = beta = 0 both splittings propagate the exit wave over
     Ns Delta exactly: the symmetric form's two half steps make one full step."""
@@ -331,11 +376,13 @@ def test_exact_transmission_from_refractive_index(oracle_lib):
     assert abs(np.angle(np.exp(k / 2j * 20.0 * (1 - n * n)) / np.exp(-1j * k * 20.0 * (delta - 1j * beta)))) > 1e-3
 
 
-@pytest.mark.parametrize("exact,strang", [(False, False), (True, False), (False, True)])
-def test_gradient_central_differences(oracle_lib, exact, strang):
+@pytest.mark.parametrize("exact,strang,angular", [(False, False, False), (True, False, False),
+                                                   (False, True, False), (False, False, True)])
+def test_gradient_central_differences(oracle_lib, exact, strang, angular):
     """dL/ddelta and dL/dbeta on a 16x16x8 sub-volume of a 32x32x16 grid."""
     ny, nz, ns = 32, 32, 16
-    geo = oracle_lib.Geometry(ny, nz, ns, alpha_i_deg=(0.3,), exact_transmission=exact, strang=strang)
+    geo = oracle_lib.Geometry(ny, nz, ns, alpha_i_deg=(0.3,), exact_transmission=exact, strang=strang,
+                              angular=angular)
     vol = ci.random_volume(11, ny, nz, ns, scale=40).astype(np.complex128)
     probe = ci.random_probe(11, 1, ny, nz).astype(np.complex128)
     I0 = oracle_lib.forward(geo, vol, probe=probe)

@@ -251,7 +251,8 @@ def run_gpu(args):
     dev = torch.device("cuda", local)
     nw, ns = args.angles, args.slices
     ckpt = checkpoint_interval(args, NY, NZ, ns, nw, dev)
-    p = B.make_params(NY, NZ, ns, angles(nw), LAM, SLICE, DY, DZ, ckpt)
+    p = B.make_params(NY, NZ, ns, angles(nw), LAM, SLICE, DY, DZ, ckpt,
+                      flags=B.MSLICE_ANGULAR if args.angular else 0)
     if not args.no_tune:
         # launch shape (blocks, column-group width, schedule) from the autotuner,
         # tuned once per device and shape outside the timed region, cached on disk
@@ -397,7 +398,8 @@ def run_gpu(args):
             "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": dict(config(nw, ns, ckpt), launch_shape={"grid_blocks": p.grid_blocks, "col_width": p.col_width,
-                                                         "schedule": p.schedule}),
+                                                         "schedule": p.schedule},
+                           propagator="angular spectrum" if args.angular else "paraxial (Eq. 1)"),
             "roofline": roofline, "effective_hbm": hbm, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
             "gpu_launches": gpu_launches, "kernels": kernels, "loss": float(loss.item())}
     print(json.dumps(line), flush=True)
@@ -894,6 +896,7 @@ def main():
     ap.add_argument("--jobs", type=int, default=64)
     ap.add_argument("--lanes", type=int, default=4, help="batch: concurrent streams, SMs split between them")
     ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--angular", action="store_true", help="sweep: angular-spectrum propagator instead of Eq. 1's")
     ap.add_argument("--lr", type=float, default=2e-6)
     ap.add_argument("--max-iters", type=int, default=300)
     args = ap.parse_args()

@@ -79,6 +79,15 @@ extern "C" {
                                          (w - w^2/2)) instead of the linearised
                                          exp(-i k Delta w); the gradient follows
                                          (d log t / dw = -i k Delta (1 - w)) */
+#define MSLICE_ANGULAR 16u  /* angular-spectrum propagator instead of the
+                               paraxial Fresnel one of Eq. 1:
+                               exp(i Delta (sqrt(k^2 - k_y^2 - k_z^2) - k)), and
+                               exp(-Delta sqrt(k_perp^2 - k^2)) exp(-i Delta k)
+                               for evanescent k_perp > k.  Not separable: the
+                               field is kept in (k_y, z) space between the row
+                               and column passes, and the run-time-size kernels
+                               run.  Not combined with MSLICE_EXIT_WAVE or
+                               MSLICE_STRANG (MSLICE_EUNSUPPORTED). */
 #define MSLICE_STRANG 8u  /* symmetric splitting of Eq. 1's slice step: half a
                              step of free propagation (Delta/2) before the first
                              slice; with MSLICE_EXIT_WAVE the last propagation is
@@ -104,7 +113,7 @@ typedef struct mslice_params {
                                   are used as given) */
     int32_t checkpoint_every;  /* adjoint segment length in slices; <= 0 means 32 */
     uint32_t flags;            /* MSLICE_EXIT_WAVE, MSLICE_PER_STRUCTURE, MSLICE_EXACT_TRANSMISSION,
-                                  MSLICE_STRANG */
+                                  MSLICE_STRANG, MSLICE_ANGULAR */
     int32_t grid_blocks;       /* launch shape: blocks of the persistent kernels, 0 = automatic
                                   (capped at the co-resident maximum) */
     int32_t col_width;         /* launch shape: columns per column-pass group (4, 8 or 16),

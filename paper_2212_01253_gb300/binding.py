@@ -23,6 +23,7 @@ MSLICE_EXIT_WAVE = 1
 MSLICE_PER_STRUCTURE = 2
 MSLICE_EXACT_TRANSMISSION = 4
 MSLICE_STRANG = 8
+MSLICE_ANGULAR = 16
 ERRORS = {-1: "MSLICE_EINVAL", -2: "MSLICE_EUNSUPPORTED", -3: "MSLICE_ELAUNCH",
           -4: "MSLICE_ETIMEDOUT", -5: "MSLICE_EWORKSPACE"}
 

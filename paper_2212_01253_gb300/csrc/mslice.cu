@@ -99,6 +99,31 @@ __global__ void k_setup(const SetupArgs S) {
     }
 }
 
+// Angular-spectrum propagator over Delta on the 2-D frequency grid, in FP64:
+// exp(i Delta (sqrt(k^2 - kp^2) - k)) = exp(-i Delta kp^2 / (sqrt(k^2 - kp^2) + k))
+// (no cancellation), and exp(-Delta sqrt(kp^2 - k^2)) exp(-i Delta k) past
+// kp = k (evanescent); stored / (ny nz) for the unnormalised transforms.
+__global__ void k_setup_p2d(float2* __restrict__ p2d, int ny, int nz, double dy, double dz, double slice,
+                            double lam) {
+    const double k = 2.0 * M_PI / lam;
+    const size_t n = (size_t)ny * nz;
+    const double inv = 1.0 / ((double)ny * (double)nz);
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const int l = (int)(i / ny), m = (int)(i % ny);
+        const int fy = (m < (ny + 1) / 2) ? m : m - ny, fz = (l < (nz + 1) / 2) ? l : l - nz;
+        const double ky = 2.0 * M_PI * fy / (ny * dy), kz = 2.0 * M_PI * fz / (nz * dz);
+        const double kp2 = ky * ky + kz * kz;
+        double s, c, amp = inv;
+        if (kp2 < k * k) {
+            sincos(-slice * kp2 / (sqrt(k * k - kp2) + k), &s, &c);
+        } else {
+            amp *= exp(-slice * sqrt(kp2 - k * k));
+            sincos(-slice * k, &s, &c);
+        }
+        p2d[i] = make_float2((float)(amp * c), (float)(amp * s));
+    }
+}
+
 // t = exp(-i k Delta (delta - i beta)) = exp(-k Delta beta) (cos(k Delta delta) - i sin(...)).
 // The phase arguments k Delta delta and k Delta beta are products with the
 // FP64 constant k Delta = kd_hi + kd_lo (two floats): fmaf(v, kd_hi, v * kd_lo)
@@ -179,8 +204,10 @@ int validate(const mslice_params* p) {
     for (int w = 0; w < p->nw; ++w)
         if (!(fabs(p->alpha_i_rad[w]) < 1.5707963)) return MSLICE_EINVAL;
     if (!(fabs(p->psi_rad) < 0.1)) return MSLICE_EINVAL;
-    if (p->flags & ~(MSLICE_EXIT_WAVE | MSLICE_PER_STRUCTURE | MSLICE_EXACT_TRANSMISSION | MSLICE_STRANG))
+    if (p->flags & ~(MSLICE_EXIT_WAVE | MSLICE_PER_STRUCTURE | MSLICE_EXACT_TRANSMISSION | MSLICE_STRANG |
+                     MSLICE_ANGULAR))
         return MSLICE_EINVAL;
+    if ((p->flags & MSLICE_ANGULAR) && (p->flags & (MSLICE_EXIT_WAVE | MSLICE_STRANG))) return MSLICE_EUNSUPPORTED;
     if (p->grid_blocks < 0 || p->col_width < 0 || p->schedule < 0 || p->schedule > 2) return MSLICE_EINVAL;
     if (p->col_width > 0 && !col_cw_ok(p->col_width, p->nz > 32 ? p->nz / 32 : 1)) return MSLICE_EINVAL;
     return MSLICE_OK;
@@ -189,6 +216,7 @@ int validate(const mslice_params* p) {
 struct Layout {
     size_t ctrl, partials, tab, probe_z, probe_y, tvol, field, gfield, gpart, ckpt, seg;
     size_t tab_half, probe_half, zero_t;  // symmetric splitting only (0 otherwise)
+    size_t p2d;                           // angular spectrum only (0 otherwise)
     size_t total;
     int K, nseg;
 };
@@ -209,6 +237,9 @@ Layout make_layout(const mslice_params* p, int op) {
     const size_t nvol = (p->flags & MSLICE_PER_STRUCTURE) ? (size_t)p->nw : 1;
     L.tvol = off; off = align256(off + nvol * p->ns * npx * sizeof(float2));
     L.field = off; off = align256(off + fb);
+    if (p->flags & MSLICE_ANGULAR) {
+        L.p2d = off; off = align256(off + npx * sizeof(float2));
+    }
     if (p->flags & MSLICE_STRANG) {
         L.tab_half = off; off = align256(off + 2 * (size_t)(p->ny + p->nz) * sizeof(float2));
         L.probe_half = off; off = align256(off + fb);
@@ -256,9 +287,22 @@ DevInfo g_dev[64];
 struct KernelSet {
     const void* fwd;
     const void* adj;
+    const void* last_far;        // k_last<C_FAR>
+    const void* last_loss;       // k_last<C_FAR_LOSS>
+    const void* last_exit;       // k_last<C_EXIT> (null with the angular spectrum)
+    const void* adj_start_seed;  // k_adj_start<true>
+    const void* adj_start;       // k_adj_start<false>
 };
 
-KernelSet sweep_kernels(int ny, int nz) {
+// the angular-spectrum propagator runs the run-time-size kernels with the
+// column pass on (k_y, k_z)
+KernelSet sweep_kernels(int ny, int nz, bool angular) {
+    if (angular)
+        return {(const void*)k_fwd_t<0, 0, true>, (const void*)k_adj_t<0, 0, true>,
+                (const void*)k_last<C_FAR, true>, (const void*)k_last<C_FAR_LOSS, true>, nullptr,
+                (const void*)k_adj_start<true, true>, (const void*)k_adj_start<false, true>};
+    const KernelSet once{nullptr, nullptr, (const void*)k_last<C_FAR>, (const void*)k_last<C_FAR_LOSS>,
+                         (const void*)k_last<C_EXIT>, (const void*)k_adj_start<true>, (const void*)k_adj_start<false>};
     ms_kernel_pair k{nullptr, nullptr};
     switch (ny) {
         case 64: k = ms_sweep_kernels_ny64(nz); break;
@@ -268,14 +312,11 @@ KernelSet sweep_kernels(int ny, int nz) {
         case 1024: k = ms_sweep_kernels_ny1024(nz); break;
         default: break;
     }
-    if (!k.fwd || !k.adj) return {(const void*)k_fwd_t<0, 0>, (const void*)k_adj_t<0, 0>};
-    return {k.fwd, k.adj};
+    KernelSet ks = once;
+    ks.fwd = k.fwd && k.adj ? k.fwd : (const void*)k_fwd_t<0, 0>;
+    ks.adj = k.fwd && k.adj ? k.adj : (const void*)k_adj_t<0, 0>;
+    return ks;
 }
-
-const void* const kOnceKernels[] = {
-    (const void*)k_last<C_FAR>, (const void*)k_last<C_FAR_LOSS>, (const void*)k_last<C_EXIT>,
-    (const void*)k_adj_start<true>, (const void*)k_adj_start<false>,
-};
 
 // raise the dynamic shared-memory limit of a kernel once per device
 constexpr int kMaxConfigured = 128;
@@ -306,10 +347,11 @@ int device_info(size_t smem, const KernelSet& ks, DevInfo** out) {
             return MSLICE_ELAUNCH;
         D.init = true;
     }
-    const void* used[7] = {ks.fwd, ks.adj};
-    for (int i = 0; i < 5; ++i) used[2 + i] = kOnceKernels[i];
+    const void* used[7] = {ks.fwd, ks.adj, ks.last_far, ks.last_loss, ks.last_exit, ks.adj_start_seed,
+                           ks.adj_start};
     int occ = 1 << 30;
     for (const void* k : used) {
+        if (!k) continue;
         int rc = configure(dev, k);
         if (rc) return rc;
         int o = 0;
@@ -428,7 +470,7 @@ int prepare(const mslice_params* p, int op, const float* vol, const float* probe
     const int cw = col_width(p);
     P->smem = smem_bytes(p->ny, p->nz, cw);
     DevInfo* D = nullptr;
-    P->ks = sweep_kernels(p->ny, p->nz);
+    P->ks = sweep_kernels(p->ny, p->nz, (p->flags & MSLICE_ANGULAR) != 0);
     if ((rc = device_info(P->smem, P->ks, &D))) return rc;
     P->grid = grid_size(p, *D);
     if (P->grid < 1) return MSLICE_EUNSUPPORTED;
@@ -490,6 +532,13 @@ int prepare(const mslice_params* p, int op, const float* vol, const float* probe
     a.per_w = (p->flags & MSLICE_PER_STRUCTURE) ? 1 : 0;
     a.lcw = ilog2(cw);
     a.split = p->nw >= 2 && p->schedule == 2;
+    if (p->flags & MSLICE_ANGULAR) {
+        const size_t n2 = (size_t)p->ny * p->nz;
+        k_setup_p2d<<<(unsigned)((n2 + 255) / 256 < 4096 ? (n2 + 255) / 256 : 4096), 256, 0, st>>>(
+            (float2*)(w + L.p2d), p->ny, p->nz, p->dy_nm, p->dz_nm, p->slice_nm, p->wavelength_nm);
+        if (note(cudaGetLastError(), "k_setup_p2d launch")) return MSLICE_ELAUNCH;
+        a.p2d = (const float2*)(w + L.p2d);
+    }
     P->tab_half = nullptr;
     if (strang) {
         // symmetric splitting: phi_0' = F^-1 P(Delta/2) F phi_0 for every
@@ -535,14 +584,14 @@ int run_gradient(const mslice_params* p, Plan& P, bool loss, cudaStream_t st) {
             if ((rc = launch_coop(P.ks.fwd, P.grid, P.smem, a, st, KID_FWD, u * (p->ns - 1)))) return rc;
         }
         a.j_end = p->ns;
-        if ((rc = launch_coop((const void*)k_last<C_FAR_LOSS>, P.grid, P.smem, a, st, KID_LAST, u))) return rc;
-        if ((rc = launch_coop((const void*)k_adj_start<false>, P.grid, P.smem, a, st, KID_ADJ_START, 0.0)))
+        if ((rc = launch_coop(P.ks.last_loss, P.grid, P.smem, a, st, KID_LAST, u))) return rc;
+        if ((rc = launch_coop(P.ks.adj_start, P.grid, P.smem, a, st, KID_ADJ_START, 0.0)))
             return rc;
     } else {
         a.j_end = p->ns;
         a.prop_last = 0;
         if ((rc = launch_coop(P.ks.fwd, P.grid, P.smem, a, st, KID_FWD, u * (p->ns - 1)))) return rc;
-        if ((rc = launch_coop((const void*)k_adj_start<true>, P.grid, P.smem, a, st, KID_ADJ_START, 0.0)))
+        if ((rc = launch_coop(P.ks.adj_start_seed, P.grid, P.smem, a, st, KID_ADJ_START, 0.0)))
             return rc;
     }
     for (int s = L.nseg - 1; s >= 0; --s) {
@@ -601,9 +650,9 @@ int mslice_forward(const mslice_params* p, const float* vol, const float* probe,
     a.j_end = p->ns;
     if (p->flags & MSLICE_EXIT_WAVE) {
         if (P.tab_half) a.tab = P.tab_half;   // the last propagation is a half step
-        return launch_coop((const void*)k_last<C_EXIT>, P.grid, P.smem, a, st, KID_LAST, u);
+        return launch_coop(P.ks.last_exit, P.grid, P.smem, a, st, KID_LAST, u);
     }
-    return launch_coop((const void*)k_last<C_FAR>, P.grid, P.smem, a, st, KID_LAST, u);
+    return launch_coop(P.ks.last_far, P.grid, P.smem, a, st, KID_LAST, u);
 }
 
 int mslice_forward_static(const mslice_params* p, const float* vol, const float* probe, float* intensity,

@@ -273,6 +273,25 @@ __device__ __forceinline__ void propagate(float2 (&x)[32], const int n, const in
     for (int m = 0; m < 32; ++m) x[m].y = -x[m].y;
 }
 
+// x <- F^-1 diag(p) F x along a column (ADJ: conj(p)), p read from the 2-D
+// angular-spectrum table: pcol[l * ny] for the column's bins l (the table
+// holds P / (ny nz); both transforms are unnormalised).
+template <bool ADJ, class SyncF>
+__device__ __forceinline__ void propagate2d(float2 (&x)[32], const int n, const int T, const int t, float2* reg,
+                                            const float2* __restrict__ Wt, const float2* __restrict__ pcol,
+                                            const int ny, const bool active, SyncF sync) {
+    const int P = n > 32 ? 32 : n;
+    fft<false>(x, n, T, t, reg, Wt, sync);
+#pragma unroll
+    for (int m = 0; m < 32; ++m) {
+        if (m < P && active) {
+            const float2 p = __ldg(pcol + (size_t)(t + T * m) * ny);
+            x[m] = ADJ ? cmulc(x[m], p) : cmul(x[m], p);
+        }
+    }
+    fft<true>(x, n, T, t, reg, Wt, sync);
+}
+
 // L2 prefetch of this block's share of [base, base + bytes): one bulk request.
 __device__ __forceinline__ void prefetch_l2(const void* base, size_t bytes) {
     if (threadIdx.x != 0 || (bytes & 15) || ((uintptr_t)base & 15)) return;
@@ -453,6 +472,7 @@ struct SweepArgs {
     int lcw;                // log2 of the columns per column-pass group
     int split;              // 1: two wavefield groups with split-phase barriers
     int exact;              // 1: exact 1 - n^2 transmission (gradient factor 1 - conj(v))
+    const float2* p2d;      // [nz][ny] angular-spectrum propagator / (ny nz) (AS kernels only)
     float scales[MSLICE_MAX_ANGLES];  // per-wavefield loss scale when per_w
 };
 
@@ -494,7 +514,13 @@ enum : int {
 #endif
 
 // ----- row pass: one team of T = ny/32 threads (1 thread for ny <= 32) per row
-template <int OP, int NC = 0>
+// AS (angular-spectrum propagator): the propagator is not separable, so it is
+// applied in the column pass on (k_y, k_z) and the field stays in (k_y, z)
+// between the passes.  The row pass of slice j > 0 first undoes the
+// y-transform of slice j-1 (unnormalised inverse; the 1/(ny nz) is in the 2-D
+// table), applies the transmission in real space and transforms along y
+// again; the adjoint runs the same steps with conj(t_j).
+template <int OP, int NC = 0, bool AS = false>
 __device__ void row_pass(const SweepArgs& A, const Smem& S, const int j, const bool first, const bool prop,
                          const int w0 = 0, int wn = 0) {
     if (wn <= 0) wn = A.nw;
@@ -515,6 +541,22 @@ __device__ void row_pass(const SweepArgs& A, const Smem& S, const int j, const b
         float2 x[32];
 #pragma unroll
         for (int m = 0; m < 32; ++m) x[m] = make_float2(0.f, 0.f);
+        // checkpoint store, transmission a = t_j phi, segment store (real space)
+        auto transmit = [&]() {
+            if ((A.flags & F_STORE_CKPT) && (j % A.K == 0)) {
+                float2* dst = A.ckpt + (size_t)(j / A.K) * A.nw * npx + row;
+#pragma unroll
+                for (int m = 0; m < 32; ++m) if (m < P) __stcg(dst + t + T * m, x[m]);
+            }
+            const float2* tv = A.tvol + vol_offset(A, w, j, z, N);
+#pragma unroll
+            for (int m = 0; m < 32; ++m) if (m < P) x[m] = cmul_t(x[m], __ldg(tv + t + T * m));
+            if (j >= A.seg_from) {
+                float2* dst = A.seg + (size_t)(j - A.seg_base) * A.nw * npx + row;
+#pragma unroll
+                for (int m = 0; m < 32; ++m) if (m < P) __stcg(dst + t + T * m, x[m]);
+            }
+        };
         if constexpr (OP == R_FWD || OP == R_FAR) {
             if (active) {
                 if (!first) {
@@ -537,25 +579,19 @@ __device__ void row_pass(const SweepArgs& A, const Smem& S, const int j, const b
                         for (int m = 0; m < 32; ++m) if (m < P) x[m] = v;
                     }
                 }
-                if ((A.flags & F_STORE_CKPT) && (j % A.K == 0)) {
-                    float2* dst = A.ckpt + (size_t)(j / A.K) * A.nw * npx + row;
-#pragma unroll
-                    for (int m = 0; m < 32; ++m) if (m < P) __stcg(dst + t + T * m, x[m]);
-                }
-                const float2* tv = A.tvol + vol_offset(A, w, j, z, N);
-#pragma unroll
-                for (int m = 0; m < 32; ++m) if (m < P) x[m] = cmul_t(x[m], __ldg(tv + t + T * m));
-                if (j >= A.seg_from) {
-                    float2* dst = A.seg + (size_t)(j - A.seg_base) * A.nw * npx + row;
-#pragma unroll
-                    for (int m = 0; m < 32; ++m) if (m < P) __stcg(dst + t + T * m, x[m]);
-                }
+                if constexpr (!AS) transmit();
+            }
+            if constexpr (AS) {
+                if (!first) fft<true>(x, N, T, t, reg, S.Wy, sync);   // uniform: back from (k_y, z)
+                if (active) transmit();
             }
             if (OP == R_FWD && !prop) continue;  // uniform
             if constexpr (OP == R_FAR) {
                 fft<false>(x, N, T, t, reg, S.Wy, sync);
 #pragma unroll
                 for (int m = 0; m < 32; ++m) x[m] = cscale(x[m], A.ffy);
+            } else if constexpr (AS) {
+                fft<false>(x, N, T, t, reg, S.Wy, sync);              // to (k_y, z)
             } else {
                 propagate<false>(x, N, T, t, reg, S.Wy, S.Py, sync);
             }
@@ -564,9 +600,8 @@ __device__ void row_pass(const SweepArgs& A, const Smem& S, const int j, const b
                 for (int m = 0; m < 32; ++m) if (m < P) __stcg(A.field + row + t + T * m, x[m]);
             }
         } else if constexpr (OP == R_ADJ) {
-            if (active) {
-#pragma unroll
-                for (int m = 0; m < 32; ++m) if (m < P) x[m] = __ldcg(A.gfield + row + t + T * m);
+            // gradient of slice j from a_j and g = g_{a_j}, then g <- conj(t_j) g
+            auto grad_back = [&]() {
                 // x = g_{a_j}; gradient contribution -i kd a_j conj(g).  The loads of
                 // a chunk of a_j are all issued before the chunk's gradient stores (the
                 // compiler may not move a load across a store it cannot prove disjoint).
@@ -621,9 +656,22 @@ __device__ void row_pass(const SweepArgs& A, const Smem& S, const int j, const b
 #pragma unroll
                     for (int m = 0; m < 32; ++m) if (m < P) x[m] = cmulc_t(x[m], __ldg(tv + t + T * m));
                 }
+            };
+            if (active) {
+#pragma unroll
+                for (int m = 0; m < 32; ++m) if (m < P) x[m] = __ldcg(A.gfield + row + t + T * m);
+                if constexpr (!AS) grad_back();
+            }
+            if constexpr (AS) {
+                fft<true>(x, N, T, t, reg, S.Wy, sync);               // uniform: back from (k_y, z)
+                if (active) grad_back();
             }
             if (!prop) continue;  // uniform
-            propagate<true>(x, N, T, t, reg, S.Wy, S.Py, sync);
+            if constexpr (AS) {
+                fft<false>(x, N, T, t, reg, S.Wy, sync);
+            } else {
+                propagate<true>(x, N, T, t, reg, S.Wy, S.Py, sync);
+            }
             if (active) {
 #pragma unroll
                 for (int m = 0; m < 32; ++m) if (m < P) __stcg(A.gfield + row + t + T * m, x[m]);
@@ -633,7 +681,9 @@ __device__ void row_pass(const SweepArgs& A, const Smem& S, const int j, const b
 #pragma unroll
                 for (int m = 0; m < 32; ++m) if (m < P) x[m] = __ldcg(A.gfield + row + t + T * m);
             }
-            fft<true>(x, N, T, t, reg, S.Wy, sync);
+            // AS: only the scale; the next adjoint row pass's inverse y-transform
+            // completes F_y^H
+            if constexpr (!AS) fft<true>(x, N, T, t, reg, S.Wy, sync);
             if (active) {
 #pragma unroll
                 for (int m = 0; m < 32; ++m) if (m < P) __stcg(A.gfield + row + t + T * m, cscale(x[m], A.ffy));
@@ -657,7 +707,7 @@ __host__ __device__ __forceinline__ bool col_cw_ok(int cw, int T) {
 __host__ __device__ __forceinline__ int col_rs(int N, int cw) { return N + N / 32 + 16 / cw; }
 
 // ----- column pass: a group of cw*T threads per cw adjacent columns
-template <int OP, int NC = 0>
+template <int OP, int NC = 0, bool AS = false>
 __device__ void col_pass(const SweepArgs& A, const Smem& S, double* s_red, const int w0 = 0, int wn = 0) {
     if (wn <= 0) wn = A.nw;
     const int N = NC ? NC : A.nz, T = row_T(N), P = N > 32 ? 32 : N;
@@ -685,7 +735,8 @@ __device__ void col_pass(const SweepArgs& A, const Smem& S, double* s_red, const
             if (active && m < P) x[m] = __ldcg(src + base + (size_t)(t + T * m) * A.ny);
         }
         if constexpr (OP == C_PROP || OP == C_EXIT || OP == C_ADJ) {
-            propagate<OP == C_ADJ>(x, N, T, t, reg, S.Wz, S.Pz, sync);
+            if constexpr (AS) propagate2d<OP == C_ADJ>(x, N, T, t, reg, S.Wz, A.p2d + col, A.ny, active, sync);
+            else propagate<OP == C_ADJ>(x, N, T, t, reg, S.Wz, S.Pz, sync);
         } else {
             if constexpr (OP != C_SEED) fft<false>(x, N, T, t, reg, S.Wz, sync);
             if constexpr (OP == C_FAR || OP == C_FAR_LOSS) {
@@ -828,7 +879,7 @@ __device__ Smem load_tables(const SweepArgs& A, float2* base) {
 // Slice loop of the forward model, j in [j_begin, j_end): Eq. 1 per slice.
 // The last slice of the range propagates only if A.prop_last.  NY, NZ: the
 // compile-time row and column lengths (0: from A).
-template <int NY, int NZ>
+template <int NY, int NZ, bool AS = false>
 __global__ void __launch_bounds__(MS_THREADS, 1) k_fwd_t(const SweepArgs A) {
     MS_KERNEL_PROLOGUE
     const size_t npx = (size_t)A.ny * A.nz;
@@ -836,14 +887,14 @@ __global__ void __launch_bounds__(MS_THREADS, 1) k_fwd_t(const SweepArgs A) {
     if (!A.split) {
         for (int j = A.j_begin; j < A.j_end; ++j) {
             const bool prop = (j < A.j_end - 1) || A.prop_last;
-            row_pass<R_FWD, NY>(A, S, j, j == A.j_begin, prop);
+            row_pass<R_FWD, NY, AS>(A, S, j, j == A.j_begin, prop);
             if (prop) {
                 if (!grid.sync()) return;
                 if (j + 1 < A.j_end) {
                     for (int w = 0; w < (A.per_w ? A.nw : 1); ++w)
                         prefetch_l2(A.tvol + (size_t)w * A.ns * npx * A.per_w + (size_t)(j + 1) * npx, slice_bytes);
                 }
-                col_pass<C_PROP, NZ>(A, S, s_red);
+                col_pass<C_PROP, NZ, AS>(A, S, s_red);
                 if (j < A.j_end - 1 && !grid.sync()) return;
             }
         }
@@ -862,7 +913,7 @@ __global__ void __launch_bounds__(MS_THREADS, 1) k_fwd_t(const SweepArgs A) {
 #pragma unroll
         for (int g = 0; g < 2; ++g) {
             if (j > A.j_begin && !grid.wait(slot[g], arr[g])) return;   // C_g(j-1) done
-            row_pass<R_FWD, NY>(A, S, j, j == A.j_begin, prop, gw0[g], gwn[g]);
+            row_pass<R_FWD, NY, AS>(A, S, j, j == A.j_begin, prop, gw0[g], gwn[g]);
             if (prop) {
                 grid.arrive(slot[g]);
                 ++arr[g];
@@ -876,7 +927,7 @@ __global__ void __launch_bounds__(MS_THREADS, 1) k_fwd_t(const SweepArgs A) {
 #pragma unroll
         for (int g = 0; g < 2; ++g) {
             if (!grid.wait(slot[g], arr[g])) return;                       // R_g(j) done
-            col_pass<C_PROP, NZ>(A, S, s_red, gw0[g], gwn[g]);
+            col_pass<C_PROP, NZ, AS>(A, S, s_red, gw0[g], gwn[g]);
             if (j < A.j_end - 1) {
                 grid.arrive(slot[g]);
                 ++arr[g];
@@ -887,14 +938,14 @@ __global__ void __launch_bounds__(MS_THREADS, 1) k_fwd_t(const SweepArgs A) {
 }
 
 // Last slice (j = ns-1) with the far field, optionally the loss and its seed.
-template <int COL>
+template <int COL, bool AS = false>
 __global__ void __launch_bounds__(MS_THREADS, 1) k_last(const SweepArgs A) {
     MS_KERNEL_PROLOGUE
     const int j = A.ns - 1;
-    if constexpr (COL == C_EXIT) row_pass<R_FWD>(A, S, j, j == A.j_begin, true);
-    else row_pass<R_FAR>(A, S, j, j == A.j_begin, true);
+    if constexpr (COL == C_EXIT) row_pass<R_FWD, 0, AS>(A, S, j, j == A.j_begin, true);
+    else row_pass<R_FAR, 0, AS>(A, S, j, j == A.j_begin, true);
     if (!grid.sync()) return;
-    col_pass<COL>(A, S, s_red);
+    col_pass<COL, 0, AS>(A, S, s_red);
     if constexpr (COL == C_FAR_LOSS) {
         if (!grid.sync()) return;
         if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -908,28 +959,28 @@ __global__ void __launch_bounds__(MS_THREADS, 1) k_last(const SweepArgs A) {
 
 // Start of the adjoint: [z-part of F_u^H on g_psi], then its y-part, so that
 // gfield = g_{a_Ns} = F_u^H g_Psi.
-template <bool SEED>
+template <bool SEED, bool AS = false>
 __global__ void __launch_bounds__(MS_THREADS, 1) k_adj_start(const SweepArgs A) {
     MS_KERNEL_PROLOGUE
     if constexpr (SEED) {
-        col_pass<C_SEED>(A, S, s_red);
+        col_pass<C_SEED, 0, AS>(A, S, s_red);
         if (!grid.sync()) return;
     }
-    row_pass<R_ADJ_FAR>(A, S, A.ns - 1, false, true);
+    row_pass<R_ADJ_FAR, 0, AS>(A, S, A.ns - 1, false, true);
     grid.finish();
 }
 
 // Adjoint slice loop, j from j_end-1 down to j_begin (a_j in the segment
 // buffer).  The transmission and a_j of the next slice are prefetched into L2
 // during the column pass.
-template <int NY, int NZ>
+template <int NY, int NZ, bool AS = false>
 __global__ void __launch_bounds__(MS_THREADS, 1) k_adj_t(const SweepArgs A) {
     MS_KERNEL_PROLOGUE
     const size_t npx = (size_t)A.ny * A.nz;
     const bool reduce = A.nw > 1 && !A.per_w;
     if (!A.split) {
         for (int j = A.j_end - 1; j >= A.j_begin; --j) {
-            row_pass<R_ADJ, NY>(A, S, j, false, j > 0);
+            row_pass<R_ADJ, NY, AS>(A, S, j, false, j > 0);
             if (!grid.sync()) return;
             if (j - 1 >= A.j_begin) {
                 for (int w = 0; w < (A.per_w ? A.nw : 1); ++w)
@@ -937,7 +988,7 @@ __global__ void __launch_bounds__(MS_THREADS, 1) k_adj_t(const SweepArgs A) {
                                 npx * sizeof(float2));
                 prefetch_l2(A.seg + (size_t)(j - 1 - A.seg_base) * A.nw * npx, A.nw * npx * sizeof(float2));
             }
-            if (j > 0) col_pass<C_ADJ, NZ>(A, S, s_red);
+            if (j > 0) col_pass<C_ADJ, NZ, AS>(A, S, s_red);
             if (reduce) reduce_gpart(A, j);
             if (j > A.j_begin && !grid.sync()) return;
         }
@@ -955,7 +1006,7 @@ __global__ void __launch_bounds__(MS_THREADS, 1) k_adj_t(const SweepArgs A) {
 #pragma unroll
         for (int g = 0; g < 2; ++g) {
             if (j < A.j_end - 1 && !grid.wait(slot[g], arr[g])) return;   // C_g(j+1) done
-            row_pass<R_ADJ, NY>(A, S, j, false, j > 0, gw0[g], gwn[g]);
+            row_pass<R_ADJ, NY, AS>(A, S, j, false, j > 0, gw0[g], gwn[g]);
             grid.arrive(slot[g]);
             ++arr[g];
         }
@@ -967,7 +1018,7 @@ __global__ void __launch_bounds__(MS_THREADS, 1) k_adj_t(const SweepArgs A) {
 #pragma unroll
         for (int g = 0; g < 2; ++g) {
             if (!grid.wait(slot[g], arr[g])) return;                        // R_g(j) done
-            if (j > 0) col_pass<C_ADJ, NZ>(A, S, s_red, gw0[g], gwn[g]);
+            if (j > 0) col_pass<C_ADJ, NZ, AS>(A, S, s_red, gw0[g], gwn[g]);
             if (g == 1 && reduce) reduce_gpart(A, j);
             if (j > A.j_begin) {
                 grid.arrive(slot[g]);

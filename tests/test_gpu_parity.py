@@ -170,6 +170,80 @@ def test_strang_per_structure_vs_oracle():
 
 
 # --------------------------------------------------------------------------
+# angular-spectrum propagator (MSLICE_ANGULAR)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("ny,nz,ns,nw,user_probe", [(64, 64, 12, 2, False), (32, 128, 5, 1, True),
+                                                     (128, 64, 7, 3, False), (32, 32, 1, 1, True),
+                                                     (512, 256, 16, 2, False)])
+def test_angular_forward_vs_oracle(ny, nz, ns, nw, user_probe):
+    """1 nm pixels, where the angular spectrum and the paraxial propagator
+    differ by 0.4-1.4 % in I."""
+    angles = np.linspace(0.15, 0.45, nw)
+    geo = oracle.Geometry(ny, nz, ns, dy_nm=1.0, dz_nm=1.0, alpha_i_deg=angles, angular=True)
+    vol = ci.random_volume(ny + 5 * ns, ny, nz, ns, scale=60)
+    probe = ci.random_probe(ny + ns, nw, ny, nz) if user_probe else None
+    I_ref = oracle.forward(geo, vol, probe=probe)
+    I = G.forward(geo, vol, probe=probe)
+    assert G.rel(I, I_ref) <= TOL_I
+    if ns > 1:
+        par = oracle.Geometry(ny, nz, ns, dy_nm=1.0, dz_nm=1.0, alpha_i_deg=angles)
+        assert G.rel(I, oracle.forward(par, vol, probe=probe)) > 10 * TOL_I
+
+
+@pytest.mark.parametrize("ny,nz,ns,nw,K,schedule", [(64, 64, 24, 1, 5, 0), (32, 64, 13, 3, 4, 0),
+                                                    (64, 128, 16, 4, 16, 2), (64, 64, 9, 2, 9, 0)])
+def test_angular_loss_grad_vs_oracle(ny, nz, ns, nw, K, schedule):
+    geo = oracle.Geometry(ny, nz, ns, dy_nm=1.0, dz_nm=1.0, alpha_i_deg=np.linspace(0.15, 0.45, nw),
+                          angular=True)
+    vol = ci.random_volume(3 * ny + ns, ny, nz, ns, scale=60)
+    meas = _target(geo, vol.astype(np.complex128) * 1.1, 6)
+    L_ref, g_ref, I_ref = oracle.loss_grad(geo, vol, meas, 0.7, return_intensity=True)
+    L, g, I = G.loss_grad(geo, vol, meas, 0.7, checkpoint_every=K, return_intensity=True, schedule=schedule)
+    assert G.rel(I, I_ref) <= TOL_I
+    assert abs(L - L_ref) <= 1e-4 * abs(L_ref)
+    assert G.rel(g, g_ref) <= TOL_GRAD
+
+
+def test_angular_per_structure_vs_oracle():
+    from paper_2212_01253_gb300 import binding as B
+    ny, nz, ns, nw = 64, 64, 9, 3
+    angles = (0.2, 0.3, 0.4)
+    vols = [ci.random_volume(500 + i, ny, nz, ns, scale=60) for i in range(nw)]
+    geos = [oracle.Geometry(ny, nz, ns, dy_nm=1.0, dz_nm=1.0, alpha_i_deg=(a,), angular=True) for a in angles]
+    meas = [_target(g, v.astype(np.complex128) * 1.1, 9 + i) for i, (g, v) in enumerate(zip(geos, vols))]
+    scales = [0.7, 1.1, 0.9]
+    p = B.make_params(ny, nz, ns, angles, dy_nm=1.0, dz_nm=1.0, checkpoint_every=4,
+                      flags=B.MSLICE_PER_STRUCTURE | B.MSLICE_ANGULAR)
+    ws = B.workspace(p, B.MSLICE_OP_LOSS_GRAD)
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    grad = torch.empty((nw, ns, nz, ny), dtype=torch.complex64, device="cuda")
+    B.mslice_loss_grad_multi(p, G.dev(np.stack(vols), np.complex64), None,
+                             G.dev(np.concatenate(meas), np.float32), scales, loss, grad, None, ws)
+    torch.cuda.synchronize()
+    assert B.mslice_status(ws) == 0
+    L_ref = 0.0
+    for i in range(nw):
+        Li, gi = oracle.loss_grad(geos[i], vols[i], meas[i], scales[i])
+        L_ref += Li
+        assert G.rel(grad[i].cpu().numpy(), gi) <= TOL_GRAD
+    assert abs(float(loss.item()) - L_ref) <= 1e-4 * abs(L_ref)
+
+
+def test_angular_rejects_exit_wave_and_strang():
+    from paper_2212_01253_gb300 import binding as B
+    for extra in (B.MSLICE_EXIT_WAVE, B.MSLICE_STRANG):
+        p = B.make_params(32, 32, 4, (0.3,), flags=B.MSLICE_ANGULAR | extra)
+        assert B._load().mslice_workspace_size(p, B.MSLICE_OP_FORWARD) == 0
+        ws = torch.empty(1 << 20, dtype=torch.uint8, device="cuda")
+        I = torch.empty((1, 32, 32), dtype=torch.float32, device="cuda")
+        F = torch.empty((1, 32, 32), dtype=torch.complex64, device="cuda")
+        v = torch.zeros((4, 32, 32), dtype=torch.complex64, device="cuda")
+        with pytest.raises(B.MsliceError) as e:
+            B.mslice_forward(p, v, None, I, F, ws)
+        assert e.value.code == -2
+
+
+# --------------------------------------------------------------------------
 # forward parity
 # --------------------------------------------------------------------------
 @pytest.mark.parametrize("seed", range(10))

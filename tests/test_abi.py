@@ -48,3 +48,30 @@ def test_workspace_size_and_validation_on_host():
         with pytest.raises(B.MsliceError):
             B.mslice_workspace_size(B.make_params(**kw), 0)
     assert B.mslice_strerror(-4).startswith("a bounded")
+
+
+def test_option_flags_size_their_buffers_and_reject_bad_combinations():
+    """Host-only: the symmetric splitting adds the half-step tables, the probe
+    copy and a zero slice; the angular spectrum adds its 2-D table; the angular
+    spectrum is not combined with the exit wave or the symmetric splitting."""
+    from paper_2212_01253_gb300 import binding as B
+    ny = nz = 64
+    ns, nw = 8, 3
+    base = B.mslice_workspace_size(B.make_params(ny, nz, ns, (0.2, 0.3, 0.4)), B.MSLICE_OP_FORWARD)
+    strang = B.mslice_workspace_size(B.make_params(ny, nz, ns, (0.2, 0.3, 0.4), flags=B.MSLICE_STRANG),
+                                     B.MSLICE_OP_FORWARD)
+    angular = B.mslice_workspace_size(B.make_params(ny, nz, ns, (0.2, 0.3, 0.4), flags=B.MSLICE_ANGULAR),
+                                      B.MSLICE_OP_FORWARD)
+    assert strang >= base + (nw + 1) * ny * nz * 8 + 2 * (ny + nz) * 8
+    assert angular >= base + ny * nz * 8
+    for extra in (B.MSLICE_EXIT_WAVE, B.MSLICE_STRANG):
+        with pytest.raises(B.MsliceError):
+            B.mslice_workspace_size(B.make_params(ny, nz, ns, flags=B.MSLICE_ANGULAR | extra), 0)
+    with pytest.raises(B.MsliceError):
+        B.mslice_workspace_size(B.make_params(ny, nz, ns, flags=1 << 10), 0)
+
+
+def test_shrinkwrap_workspace_size_on_host(lib):
+    lib.mslice_shrinkwrap_workspace.restype = ctypes.c_size_t
+    lib.mslice_shrinkwrap_workspace.argtypes = [ctypes.c_size_t]
+    assert lib.mslice_shrinkwrap_workspace(216) >= 2 * 216 * 4

@@ -80,7 +80,7 @@ def build(force: bool = False, verbose: bool = False, jobs: int | None = None) -
             print("==", os.path.basename(obj))
             print(out)
     tmp = LIB + ".tmp%d" % os.getpid()
-    subprocess.check_call([cc, *ARCH, "-shared", "-o", tmp] + [o for o, _ in results])
+    subprocess.check_call([cc, *ARCH, "-shared", "-o", tmp] + [o for o, _ in results] + ["-ldl"])
     os.replace(tmp, LIB)
     return LIB
 

@@ -10,6 +10,8 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "mslice.h"
 #include "mslice_device.cuh"
 #include "mslice_kernels.h"
@@ -425,7 +427,18 @@ int launch_coop(const void* fn, int grid, size_t smem, const SweepArgs& a, cudaS
                 double units) {
     void* args[] = {(void*)&a};
     ProfRec* r = prof_begin(kid, units, st);
+    // host-side range named after the kernel (slice range in the payload), for
+    // profilers that attach an NVTX tool; a no-op otherwise
+    nvtxEventAttributes_t ev{};
+    ev.version = NVTX_VERSION;
+    ev.size = NVTX_EVENT_ATTRIB_STRUCT_SIZE;
+    ev.messageType = NVTX_MESSAGE_TYPE_ASCII;
+    ev.message.ascii = kKernelNames[kid];
+    ev.payloadType = NVTX_PAYLOAD_TYPE_INT32;
+    ev.payload.iValue = a.j_begin;
+    nvtxRangePushEx(&ev);
     cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(MS_THREADS), args, smem, st);
+    nvtxRangePop();
     prof_end(r, st);
     return note(e, "cudaLaunchCooperativeKernel") ? MSLICE_ELAUNCH : MSLICE_OK;
 }

@@ -68,6 +68,28 @@ class Reconstructor:
         if self.snap_every and self.snap_levels and self.t >= self.snap_start and self.t % self.snap_every == 0:
             B.mslice_snap(self.theta, self.snap_levels)
 
+    def save(self, path):
+        """Write theta, the ADAM moments and the iteration count to `path`
+        (.npz), so that a later Reconstructor resumes exactly where this one
+        stopped (the fixed part of the volume, the target and the settings are
+        the caller's to rebuild)."""
+        import numpy as np
+        torch.cuda.synchronize()
+        np.savez(path, theta=self.theta.cpu().numpy(), m=self.m.cpu().numpy(), v=self.v.cpu().numpy(),
+                 t=np.int64(self.t))
+
+    def load(self, path):
+        """Resume from a file written by `save`."""
+        import numpy as np
+        d = np.load(path)
+        for name in ("theta", "m", "v"):
+            src = torch.from_numpy(d[name])
+            if src.numel() != self.theta.numel():
+                raise ValueError("%s in %s has %d values, expected %d" % (name, path, src.numel(),
+                                                                          self.theta.numel()))
+            getattr(self, name).copy_(src.to(self.theta.device))
+        self.t = int(d["t"])
+
     def chi2(self):
         return 4.0 * float(self.loss.item()) / self.npix
 

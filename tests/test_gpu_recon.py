@@ -107,3 +107,35 @@ def test_coarse_map_with_host_material_and_snapping_vs_oracle():
     th = G.dev(theta, np.float32)
     B.mslice_snap(th, [0.0, float(np.float32(d_au))])
     np.testing.assert_array_equal(th.cpu().numpy(), oracle.snap(theta, [0.0, float(np.float32(d_au))]))
+
+
+def test_reconstruction_resumes_from_a_saved_state_bit_for_bit(tmp_path):
+    """Six iterations in one go equal three, save, a fresh Reconstructor that
+    loads the file, and three more: theta and the ADAM moments bit for bit."""
+    from paper_2212_01253_gb300 import binding as B
+    from paper_2212_01253_gb300.recon import Reconstructor
+    ny = nz = 64
+    ns = 32
+    shape, block, off = (4, 8, 8), (8, 4, 8), (0, 32, 0)
+    geo = oracle.Geometry(ny, nz, ns, alpha_i_deg=(0.3,))
+    rng = np.random.default_rng(21)
+    truth = (rng.random(shape) < 0.3).astype(np.float64) * 4.7e-5
+    base = ci.substrate(ny, nz, ns)
+    I_gt = oracle.forward(geo, oracle.coarse_to_fine(truth, (ns, nz, ny), block, off, base=base))
+    meas, s = ci.poisson_target(I_gt, 1e6, seed=4)
+    args = (G.params(geo), B.make_coarse(shape, block, off), G.dev(base, np.complex64), G.dev(meas, np.float32), s)
+    one = Reconstructor(*args, lr=2e-6, snap_every=4, snap_levels=(0.0, 4.7e-5))
+    for _ in range(6):
+        one.step()
+    first = Reconstructor(*args, lr=2e-6, snap_every=4, snap_levels=(0.0, 4.7e-5))
+    for _ in range(3):
+        first.step()
+    first.save(tmp_path / "state.npz")
+    second = Reconstructor(*args, lr=2e-6, snap_every=4, snap_levels=(0.0, 4.7e-5))
+    second.load(tmp_path / "state.npz")
+    assert second.t == 3
+    for _ in range(3):
+        second.step()
+    torch.cuda.synchronize()
+    for name in ("theta", "m", "v"):
+        assert torch.equal(getattr(one, name), getattr(second, name)), name

@@ -229,6 +229,25 @@ def test_angular_per_structure_vs_oracle():
     assert abs(float(loss.item()) - L_ref) <= 1e-4 * abs(L_ref)
 
 
+@pytest.mark.parametrize("opts", [dict(exact_transmission=True, strang=True, psi_deg=0.35),
+                                  dict(exact_transmission=True, angular=True, psi_deg=-0.5),
+                                  dict(strang=True, psi_deg=0.2)])
+def test_option_combinations_loss_grad_vs_oracle(opts):
+    """The options together: each changes its own step, and none disturbs
+    another (the half-step probe of the symmetric splitting starts from the
+    psi-tilted default probe; the angular spectrum keeps the exact
+    transmission's gradient factor)."""
+    ny, nz, ns, nw = 64, 64, 12, 2
+    geo = oracle.Geometry(ny, nz, ns, dy_nm=1.0, dz_nm=1.0, alpha_i_deg=(0.2, 0.4), **opts)
+    vol = ci.random_volume(77, ny, nz, ns, scale=60)
+    meas = _target(geo, vol.astype(np.complex128) * 1.1, 3)
+    L_ref, g_ref, I_ref = oracle.loss_grad(geo, vol, meas, 0.8, return_intensity=True)
+    L, g, I = G.loss_grad(geo, vol, meas, 0.8, checkpoint_every=5, return_intensity=True)
+    assert G.rel(I, I_ref) <= TOL_I
+    assert abs(L - L_ref) <= 1e-4 * abs(L_ref)
+    assert G.rel(g, g_ref) <= TOL_GRAD
+
+
 def test_angular_rejects_exit_wave_and_strang():
     from paper_2212_01253_gb300 import binding as B
     for extra in (B.MSLICE_EXIT_WAVE, B.MSLICE_STRANG):

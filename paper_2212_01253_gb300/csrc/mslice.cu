@@ -443,6 +443,16 @@ int launch_coop(const void* fn, int grid, size_t smem, const SweepArgs& a, cudaS
     return note(e, "cudaLaunchCooperativeKernel") ? MSLICE_ELAUNCH : MSLICE_OK;
 }
 
+// streaming multiprocessors of the current device (cached; 152 on GB300)
+int device_sms() {
+    static int cache[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+    if (cache[dev] <= 0 && cudaDeviceGetAttribute(&cache[dev], cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return 152;
+    return cache[dev] > 0 ? cache[dev] : 152;
+}
+
 int launch_transmission(const float2* vol, float2* tv, size_t nvox, double kd, int exact, int minus_one,
                         cudaStream_t st) {
     const float kd_hi = (float)kd;
@@ -450,7 +460,8 @@ int launch_transmission(const float2* vol, float2* tv, size_t nvox, double kd, i
     const size_t n2 = nvox / 2;
     if (n2) {
         size_t tb = (n2 + 255) / 256;
-        if (tb > 152 * 16) tb = 152 * 16;
+        const size_t cap = (size_t)device_sms() * 16;   // 16 resident 256-thread blocks per SM
+        if (tb > cap) tb = cap;
         k_transmission<<<(unsigned)tb, 256, 0, st>>>((const float4*)vol, (float4*)tv, n2, kd_hi, kd_lo, exact, minus_one);
         if (note(cudaGetLastError(), "k_transmission launch")) return MSLICE_ELAUNCH;
     }

@@ -352,14 +352,22 @@ unsigned nb(size_t n) {
     return (unsigned)(b > 4096 ? 4096 : (b ? b : 1));
 }
 
-constexpr int kTargetCtas = 304;  // two waves' worth of 64x64 tiles on 152 SMs
+// two waves' worth of 64x64 tiles: twice the SM count of the current device
+int target_ctas() {
+    static int cache[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 304;
+    if (cache[dev] <= 0 && cudaDeviceGetAttribute(&cache[dev], cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return 304;
+    return cache[dev] > 0 ? 2 * cache[dev] : 304;
+}
 constexpr int kMaxSplits = 64;
 
 // split-K factor: enough CTAs to cover the GPU, at least 4 k-steps per split
 int gemm_splits(int M, int N, int K) {
     const long tiles = (long)((M + kTM - 1) / kTM) * ((N + kTN - 1) / kTN);
     const int ksteps = (K + kTK - 1) / kTK;
-    long s = (kTargetCtas + tiles - 1) / tiles;
+    long s = (target_ctas() + tiles - 1) / tiles;
     s = s < ksteps / 4 ? s : ksteps / 4;
     s = s < kMaxSplits ? s : kMaxSplits;
     return s < 1 ? 1 : (int)s;

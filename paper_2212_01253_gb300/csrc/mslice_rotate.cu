@@ -212,6 +212,15 @@ int make_map(const mslice_params* p, double alpha, double psi, const double* c, 
     return MSLICE_OK;
 }
 
+int device_sms() {
+    static int cache[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+    if (cache[dev] <= 0 && cudaDeviceGetAttribute(&cache[dev], cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return 152;
+    return cache[dev] > 0 ? cache[dev] : 152;
+}
+
 int launch(const mslice_params* p, double alpha, double psi, const double* c, const float* in, float* out,
            bool adjoint, void* stream) {
     RotMap R;
@@ -221,7 +230,8 @@ int launch(const mslice_params* p, double alpha, double psi, const double* c, co
     cudaStream_t st = (cudaStream_t)stream;
     const size_t n = (size_t)p->ns * p->nz * p->ny;
     const long long rows = (long long)p->ns * p->nz;
-    const unsigned blocks = (unsigned)(rows / 8 + 1 < 152 * 32 ? rows / 8 + 1 : 152 * 32);
+    const long long cap = (long long)device_sms() * 32;   // a few waves of 8-warp blocks per SM
+    const unsigned blocks = (unsigned)(rows / 8 + 1 < cap ? rows / 8 + 1 : cap);
     if (adjoint) {
         if (cudaMemsetAsync(out, 0, n * sizeof(float2), st) != cudaSuccess) return MSLICE_ELAUNCH;
         k_rotate<true><<<blocks, 256, 0, st>>>((const float2*)in, (float2*)out, R);

@@ -317,14 +317,16 @@ def run_gpu(args):
         # end to end from pinned host memory through the public API: every step
         # copies its volume and targets in and its gradient and loss out; the
         # copies of one step overlap the slice loop of its neighbours
-        # (HostPipeline: copy-in, compute and copy-out streams, two device slots)
+        # (HostPipeline: copy-in, compute and copy-out streams, two device
+        # slots; three, which let a step's copy-in and the previous step's
+        # copy-out run at once, measured no faster)
         from paper_2212_01253_gb300.pipeline import HostPipeline
-        pipe = HostPipeline(p, s, dev)
+        pipe = HostPipeline(p, s, dev, slots=2)
         vol_pin = torch.from_numpy(vol_h).pin_memory()
         meas_pin = torch.from_numpy(meas_h).pin_memory()
         grad_pin = [torch.empty(grad.shape, dtype=grad.dtype).pin_memory() for _ in range(2)]
         loss_pin = [torch.empty(1, dtype=torch.float64).pin_memory() for _ in range(2)]
-        for k in range(2):
+        for k in range(len(pipe.slots)):
             pipe.submit(vol_pin, meas_pin, grad_pin[k % 2], loss_pin[k % 2])
         torch.cuda.synchronize()
         if world > 1:

@@ -4,7 +4,7 @@ copies of one problem overlapping the GPU work of its neighbours.
 A caller whose volumes and detector images sit in (pinned) host memory, and
 who needs each gradient back on the host, would otherwise pay the copies in
 series with the slice loop: at 512x512x1024 with 9 angles that is 2.2 GB in and
-2.1 GB out per problem.  `HostPipeline` keeps two device slots and three
+2.1 GB out per problem.  `HostPipeline` keeps `slots` device slots and three
 streams:
 
     copy-in stream   vol, meas  -> slot b          (waits until slot b's last
@@ -13,6 +13,9 @@ streams:
     copy-out stream  grad, loss -> host            (waits for its compute)
 
 so problem k+1 is copied in and problem k-1 copied out while problem k runs.
+With two slots the copy-in of k+1 reuses k-1's slot and waits for its
+copy-out, so the two copies run one after the other; with three they run at
+once, on the two copy directions.
 Ordering between the streams is by CUDA events only; the host never blocks
 unless it asks for a result.  The arithmetic is exactly `mslice_loss_grad`'s.
 """

@@ -1,4 +1,4 @@
-"""HostPipeline (copies on their own streams, two device slots) gives the same
+"""HostPipeline (copies on their own streams, two or three device slots) gives the same
 loss and gradient as mslice_loss_grad on device tensors, bit for bit, for a
 sequence of different host-resident problems."""
 import numpy as np
@@ -18,14 +18,15 @@ def _built():
     build.build()
 
 
-def test_host_pipeline_matches_device_calls():
+@pytest.mark.parametrize("slots", [2, 3])
+def test_host_pipeline_matches_device_calls(slots):
     from paper_2212_01253_gb300 import binding as B
     from paper_2212_01253_gb300.pipeline import HostPipeline
     geo = oracle.Geometry(128, 64, 20, alpha_i_deg=(0.2, 0.35))
     p = G.params(geo, checkpoint_every=8)
     vols = [ci.random_volume(40 + k, 128, 64, 20, scale=40) for k in range(5)]
     meas = (np.sqrt(oracle.forward(geo, vols[0])) * 1.1).astype(np.float32)
-    pipe = HostPipeline(p, 0.8)
+    pipe = HostPipeline(p, 0.8, slots=slots)
     meas_pin = torch.from_numpy(meas).pin_memory()
     outs = []
     for v in vols:

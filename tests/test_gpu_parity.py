@@ -347,7 +347,9 @@ def _target(geo, vol, seed):
 
 
 @pytest.mark.parametrize("ny,nz,ns,nw,K", [(64, 64, 32, 1, 32), (64, 64, 32, 1, 5), (32, 64, 13, 3, 4),
-                                           (128, 32, 20, 2, 7), (16, 16, 1, 1, 32), (8, 256, 9, 1, 1)])
+                                           (128, 32, 20, 2, 7), (16, 16, 1, 1, 32), (8, 256, 9, 1, 1),
+                                           (1024, 64, 3, 1, 3), (64, 1024, 3, 2, 2), (1, 64, 5, 1, 2),
+                                           (64, 1, 5, 1, 5), (2, 2, 4, 1, 2), (32, 32, 4, 16, 3)])
 def test_loss_grad_vs_oracle(ny, nz, ns, nw, K):
     geo = oracle.Geometry(ny, nz, ns, alpha_i_deg=np.linspace(0.15, 0.45, nw))
     vol = ci.random_volume(ny + nz + ns, ny, nz, ns, scale=40)

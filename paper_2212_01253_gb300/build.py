@@ -48,7 +48,11 @@ def _units():
     units = [(os.path.join(CSRC, "mslice.cu"), os.path.join(BUILD_DIR, "mslice.o"), inc),
              (os.path.join(CSRC, "mslice_recon.cu"), os.path.join(BUILD_DIR, "mslice_recon.o"), inc),
              (os.path.join(CSRC, "mslice_nn.cu"), os.path.join(BUILD_DIR, "mslice_nn.o"), inc),
-             (os.path.join(CSRC, "mslice_rotate.cu"), os.path.join(BUILD_DIR, "mslice_rotate.o"), inc)]
+             (os.path.join(CSRC, "mslice_rotate.cu"), os.path.join(BUILD_DIR, "mslice_rotate.o"), inc),
+             (os.path.join(CSRC, "mslice_generic.cu"), os.path.join(BUILD_DIR, "generic_paraxial.o"),
+              inc + ["-DMS_AS=0"]),
+             (os.path.join(CSRC, "mslice_generic.cu"), os.path.join(BUILD_DIR, "generic_angular.o"),
+              inc + ["-DMS_AS=1"])]
     for ny in ROW_LENGTHS:
         units.append((os.path.join(CSRC, "mslice_inst.cu"), os.path.join(BUILD_DIR, "inst_ny%d.o" % ny),
                       inc + ["-DMS_NY=%d" % ny]))

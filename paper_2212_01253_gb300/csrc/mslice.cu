@@ -286,25 +286,14 @@ DevInfo g_dev[64];
 
 // persistent kernels used by one call: the slice loops (size-specialised when
 // an instance exists, generic otherwise) and the once-per-call kernels
-struct KernelSet {
-    const void* fwd;
-    const void* adj;
-    const void* last_far;        // k_last<C_FAR>
-    const void* last_loss;       // k_last<C_FAR_LOSS>
-    const void* last_exit;       // k_last<C_EXIT> (null with the angular spectrum)
-    const void* adj_start_seed;  // k_adj_start<true>
-    const void* adj_start;       // k_adj_start<false>
-};
+using KernelSet = ms_kernel_set;
 
 // the angular-spectrum propagator runs the run-time-size kernels with the
-// column pass on (k_y, k_z)
+// column pass on (k_y, k_z); the paraxial one the size-specialised instance
+// when there is one
 KernelSet sweep_kernels(int ny, int nz, bool angular) {
-    if (angular)
-        return {(const void*)k_fwd_t<0, 0, true>, (const void*)k_adj_t<0, 0, true>,
-                (const void*)k_last<C_FAR, true>, (const void*)k_last<C_FAR_LOSS, true>, nullptr,
-                (const void*)k_adj_start<true, true>, (const void*)k_adj_start<false, true>};
-    const KernelSet once{nullptr, nullptr, (const void*)k_last<C_FAR>, (const void*)k_last<C_FAR_LOSS>,
-                         (const void*)k_last<C_EXIT>, (const void*)k_adj_start<true>, (const void*)k_adj_start<false>};
+    if (angular) return ms_generic_kernels_angular();
+    KernelSet ks = ms_generic_kernels_paraxial();
     ms_kernel_pair k{nullptr, nullptr};
     switch (ny) {
         case 64: k = ms_sweep_kernels_ny64(nz); break;
@@ -314,9 +303,10 @@ KernelSet sweep_kernels(int ny, int nz, bool angular) {
         case 1024: k = ms_sweep_kernels_ny1024(nz); break;
         default: break;
     }
-    KernelSet ks = once;
-    ks.fwd = k.fwd && k.adj ? k.fwd : (const void*)k_fwd_t<0, 0>;
-    ks.adj = k.fwd && k.adj ? k.adj : (const void*)k_adj_t<0, 0>;
+    if (k.fwd && k.adj) {
+        ks.fwd = k.fwd;
+        ks.adj = k.adj;
+    }
     return ks;
 }
 

@@ -1,7 +1,11 @@
-// mslice_kernels.h -- size-specialised slice-loop kernels, one translation unit
-// per row length ny (mslice_inst.cu compiled with -DMS_NY=ny).  Each function
-// returns the forward and adjoint slice-loop kernels for column length nz, or
-// null pointers if that pair has no specialised instance.
+// mslice_kernels.h -- the slice-loop kernels, instantiated in translation
+// units of their own so that they compile in parallel:
+//   mslice_inst.cu (one unit per row length ny, -DMS_NY=ny): size-specialised
+//     forward and adjoint kernels for each column length nz, or null pointers
+//     if that pair has no specialised instance;
+//   mslice_generic.cu (-DMS_AS=0 and -DMS_AS=1): the run-time-size kernels and
+//     the once-per-call kernels, for the paraxial propagator and for the
+//     angular spectrum.
 #pragma once
 
 struct ms_kernel_pair {
@@ -14,3 +18,16 @@ ms_kernel_pair ms_sweep_kernels_ny128(int nz);
 ms_kernel_pair ms_sweep_kernels_ny256(int nz);
 ms_kernel_pair ms_sweep_kernels_ny512(int nz);
 ms_kernel_pair ms_sweep_kernels_ny1024(int nz);
+
+struct ms_kernel_set {
+    const void* fwd;             // k_fwd_t
+    const void* adj;             // k_adj_t
+    const void* last_far;        // k_last<C_FAR>
+    const void* last_loss;       // k_last<C_FAR_LOSS>
+    const void* last_exit;       // k_last<C_EXIT> (null with the angular spectrum)
+    const void* adj_start_seed;  // k_adj_start<true>
+    const void* adj_start;       // k_adj_start<false>
+};
+
+ms_kernel_set ms_generic_kernels_paraxial();
+ms_kernel_set ms_generic_kernels_angular();

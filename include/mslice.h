@@ -270,7 +270,10 @@ int mslice_snap(float *theta, size_t n, const float *levels, int nlevels, void *
  * The blur takes its taps in order with FP32 products and sums rounded one by
  * one (no fused multiply-add), so the support is reproducible bit for bit.
  * kept: NULL or a device int that receives the support's size.  ws: device
- * workspace, 16-byte aligned, of mslice_shrinkwrap_workspace(cx*cz*cy) bytes. */
+ * workspace, 16-byte aligned, of mslice_shrinkwrap_workspace(cx*cz*cy) bytes,
+ * owned by the caller.  Returns MSLICE_EINVAL for a null theta or ws, a
+ * non-positive grid size or sigma, a threshold outside [0, 1] or a short or
+ * misaligned workspace; MSLICE_ELAUNCH when a launch fails. */
 size_t mslice_shrinkwrap_workspace(size_t n);
 int mslice_shrinkwrap(float *theta, int cx, int cz, int cy, float sigma, float threshold, int *kept, void *ws,
                       size_t ws_bytes, void *stream);
@@ -303,13 +306,19 @@ int mslice_adam_step(float *theta, float *m, float *v, const float *grad, size_t
  * (the volume extends past its faces by its edge values).
  * ------------------------------------------------------------------------ */
 
-/* vol_lab = R vol_sample.  Device buffers, no aliasing; asynchronous on stream. */
+/* vol_lab = R vol_sample.  Device buffers owned by the caller, 8-byte
+ * aligned, not aliased; asynchronous on stream.  Returns MSLICE_EINVAL for a
+ * null or misaligned pointer, vol_sample == vol_lab, a non-positive spacing,
+ * a size outside [1, MSLICE_MAX_N] across the beam or ns < 1, or a non-finite
+ * angle or centre; MSLICE_EUNSUPPORTED when ns * nz >= 2^31 or a sample
+ * index would leave +-2^30; MSLICE_ELAUNCH when the launch fails. */
 int mslice_rotate(const mslice_params *p, double alpha_rad, double psi_rad, const double *center_nm,
                   const float *vol_sample, float *vol_lab, void *stream);
 
 /* g_sample = R^T g_lab (overwritten): the lab-frame gradient scattered back
  * with the interpolation weights.  Summed with float atomics, so the result
- * is not bitwise reproducible from run to run. */
+ * is not bitwise reproducible from run to run.  Buffers and errors as for
+ * mslice_rotate. */
 int mslice_rotate_adjoint(const mslice_params *p, double alpha_rad, double psi_rad, const double *center_nm,
                           const float *g_lab, float *g_sample, void *stream);
 

@@ -19,6 +19,25 @@ from . import autotune
 from . import binding as B
 
 
+def assign_lanes(costs, lanes):
+    """Greedy longest-first assignment of jobs with the given costs to `lanes`
+    queues, each job onto the least loaded queue (ties: the lowest index).
+    Returns the job indices of each queue, in the order they were placed."""
+    out = [[] for _ in range(max(1, int(lanes)))]
+    load = [0.0] * len(out)
+    for i in sorted(range(len(costs)), key=lambda i: (-costs[i], i)):
+        k = load.index(min(load))
+        out[k].append(i)
+        load[k] += costs[i]
+    return out
+
+
+def group_cost(p):
+    """Modelled time of one group's loss + gradient: its work plus a per-slice
+    latency term (grid barriers and launch-bound slice steps)."""
+    return p.nw * p.ny * p.nz * p.ns / 4e10 + p.ns * 2.5e-5
+
+
 class BatchedLossGrad:
     def __init__(self, jobs, wavelength_nm=0.155, slice_nm=20.0, dy_nm=2.0, dz_nm=2.0, checkpoint_every=32,
                  tune=True, device="cuda", lanes=1):
@@ -57,15 +76,8 @@ class BatchedLossGrad:
                 self.groups.append(g)
         self.graph = None
         self.units = sum(g["p"].nw * g["p"].ny * g["p"].nz * g["p"].ns for g in self.groups)
-        # groups to lanes, longest first onto the least loaded lane (cost: work
-        # plus a per-slice latency term)
-        self.lanes = [[] for _ in range(max(1, int(lanes)))]
-        load = [0.0] * len(self.lanes)
-        cost = lambda g: g["p"].nw * g["p"].ny * g["p"].nz * g["p"].ns / 4e10 + g["p"].ns * 2.5e-5
-        for gi in sorted(range(len(self.groups)), key=lambda i: -cost(self.groups[i])):
-            k = load.index(min(load))
-            self.lanes[k].append(gi)
-            load[k] += cost(self.groups[gi])
+        # groups to lanes, longest first onto the least loaded lane
+        self.lanes = assign_lanes([group_cost(g["p"]) for g in self.groups], lanes)
         self.streams = [torch.cuda.Stream(self.device) for _ in self.lanes] if len(self.lanes) > 1 else []
 
     def _enqueue(self, g, stream=None):

@@ -390,8 +390,12 @@ def test_split_phase_schedule_is_bitwise_identical(ny, nz, ns, nw, K):
     assert L1 == L2 and np.array_equal(g1, g2) and np.array_equal(J1, J2)
 
 
-def test_adjoint_vs_oracle():
-    geo = oracle.Geometry(64, 32, 10, alpha_i_deg=(0.2, 0.35))
+@pytest.mark.parametrize("opts", [dict(), dict(angular=True, dy_nm=1.0, dz_nm=1.0), dict(strang=True),
+                                  dict(exact_transmission=True, psi_deg=0.3)])
+def test_adjoint_vs_oracle(opts):
+    """mslice_adjoint for a given detector gradient (the autograd path), with
+    each propagator and splitting option."""
+    geo = oracle.Geometry(64, 32, 10, alpha_i_deg=(0.2, 0.35), **opts)
     vol = ci.random_volume(31, 64, 32, 10, scale=40)
     rng = np.random.default_rng(31)
     gpsi = (rng.normal(size=(2, 32, 64)) + 1j * rng.normal(size=(2, 32, 64))).astype(np.complex64)

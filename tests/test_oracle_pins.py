@@ -499,3 +499,38 @@ def test_in_plane_angle_plane_wave_lands_in_one_bin(oracle_lib):
     assert I[0, 0, ny - m] == pytest.approx(ny * nz, rel=1e-12)
     assert I.sum() == pytest.approx(ny * nz, rel=1e-12)
     assert I[0, 0, m] < 1e-20
+
+
+# --------------------------------------------------------------------------
+# The 1-D propagator tables P_y, P_z (Eq. 1's "C" of Fig. 1)
+# --------------------------------------------------------------------------
+def test_propagator_tables_move_a_basis_mode_by_their_product(oracle_lib):
+    """Eq. 1: one DFT basis mode exp(2 pi i (a m / ny + b l / nz)) through one
+    vacuum slice (exit wave, so the propagation is applied once) comes back as
+    itself times P(k_y[a], k_z[b]) = exp(-i Delta (k_y^2 + k_z^2) / 2k).  The
+    slice loop builds its own 2-D table (pinned to the analytic Fresnel beam
+    above), so the mode's phase fixes P_y[a] P_z[b] from separate code.  The
+    axes have different lengths and pixel sizes (ny != nz, dy != dz), so a
+    swapped axis or spacing, a missing factor 2 or a sign error fails."""
+    ny, nz, dy, dz, delta = 32, 8, 2.0, 0.5, 300.0
+    geo = oracle_lib.Geometry(ny, nz, 1, slice_nm=delta, dy_nm=dy, dz_nm=dz, alpha_i_deg=(0.0,))
+    py, pz = oracle_lib.propagator_1d(geo)
+    assert py.shape == (ny,) and pz.shape == (nz,)
+    # unit modulus, even in k (P[f] = P[-f]), 1 at k = 0
+    assert np.abs(np.abs(py) - 1).max() < 1e-14 and np.abs(np.abs(pz) - 1).max() < 1e-14
+    assert py[0] == 1 and pz[0] == 1
+    assert np.abs(py[1:] - py[1:][::-1]).max() < 1e-14
+    assert np.abs(pz[1:] - pz[1:][::-1]).max() < 1e-14
+    m = np.arange(ny)[None, :]
+    l = np.arange(nz)[:, None]
+    for a, b in [(1, 0), (0, 1), (3, 2), (ny - 5, nz - 3), (ny // 2, nz // 2), (7, 0), (0, nz - 1)]:
+        mode = np.exp(2j * np.pi * (a * m / ny + b * l / nz))
+        out = oracle_lib.forward(geo, np.zeros((1, nz, ny)), probe=mode[None], exit_wave=True)[0]
+        # the frequency of bin a in cycles per nm, with the sign numpy's fftfreq gives
+        fy = (a if a < ny / 2 else a - ny) / (ny * dy)
+        fz = (b if b < nz / 2 else b - nz) / (nz * dz)
+        closed = np.exp(-1j * delta * LAM * np.pi * (fy * fy + fz * fz))   # Delta (2 pi f)^2 / 2k
+        assert np.abs(out - closed * mode).max() < 1e-12, (a, b)
+        assert abs(py[a] * pz[b] - closed) < 1e-13, (a, b)
+        assert abs(py[a] - np.exp(-1j * delta * LAM * np.pi * fy * fy)) < 1e-13
+        assert abs(pz[b] - np.exp(-1j * delta * LAM * np.pi * fz * fz)) < 1e-13

@@ -35,6 +35,8 @@
  *   `stream` (a cudaStream_t, NULL = legacy default stream) and is asynchronous;
  *   outputs are valid once the stream reaches them.  Outputs must not alias
  *   inputs or the workspace.  Calls sharing one workspace must not overlap.
+ *   The one exception is mslice_forward_static(), whose workspace is a fixed
+ *   device array owned by the library itself (declared below).
  *
  * Errors: functions return MSLICE_OK (0) or a negative MSLICE_E* code; they never
  * abort or trap.  Device-side waits are bounded: a wait that runs out marks the
@@ -149,13 +151,22 @@ int mslice_forward(const mslice_params *p, const float *vol, const float *probe,
  * rejected with MSLICE_EWORKSPACE (32 MiB covers e.g. 512x512 x 14 slices or
  * 256x256 x 60 slices).  The first call on a device looks up the array's
  * device address (cudaGetSymbolAddress, with that device current); make that
- * first call before any stream capture.  Every call shares the one array and
- * leaves its last contents there (the control words are cleared at the start
- * of each call): calls that overlap on the GPU -- on different streams, or
- * from different host threads -- race and must not be issued.  Other
- * arguments and errors as for mslice_forward. */
+ * first call before any stream capture.  The looked-up address is kept for
+ * the life of the process: after a cudaDeviceReset of that device, or an
+ * unload and reload of the library, it is stale, and the library must be
+ * reloaded.  Device indices of 64 and above get MSLICE_EUNSUPPORTED.  Every
+ * call shares the one array and leaves its last contents there (the control
+ * words are cleared at the start of each call): calls that overlap on the
+ * GPU -- on different streams, or from different host threads -- race and
+ * must not be issued.  Other arguments and errors as for mslice_forward. */
 int mslice_forward_static(const mslice_params *p, const float *vol, const float *probe,
                           float *intensity, float *field_out, void *stream);
+
+/* mslice_status() for the library-owned workspace of mslice_forward_static on
+ * the current device: waits for `stream`, then returns MSLICE_OK, or
+ * MSLICE_ETIMEDOUT if a bounded device-side wait of the last static call ran
+ * out (its intensities are then not valid).  Allocates nothing. */
+int mslice_forward_static_status(void *stream);
 
 /* Gradient of a real loss through the forward model, for a given detector
  * gradient (replaces the autograd backward of Sec. 3-4).

@@ -121,6 +121,7 @@ def _load():
                 "mslice_workspace_size": ([P, ctypes.c_int], sz),
                 "mslice_forward": ([P, vp, vp, vp, vp, vp, sz, vp], ctypes.c_int),
                 "mslice_forward_static": ([P, vp, vp, vp, vp, vp], ctypes.c_int),
+                "mslice_forward_static_status": ([vp], ctypes.c_int),
                 "mslice_adjoint": ([P, vp, vp, vp, vp, vp, sz, vp], ctypes.c_int),
                 "mslice_loss_grad": ([P, vp, vp, vp, ctypes.c_float, vp, vp, vp, vp, sz, vp],
                                      ctypes.c_int),
@@ -239,6 +240,12 @@ def mslice_forward_static(p, vol, probe, intensity, field_out, stream=None):
         _ptr(probe, torch.complex64, nfield, "probe"),
         _ptr(intensity, torch.float32, nfield, "intensity"),
         _ptr(field_out, torch.complex64, nfield, "field_out"), _stream(stream)), "mslice_forward_static")
+
+
+def mslice_forward_static_status(stream=None) -> int:
+    """0, or a negative code (-4 = MSLICE_ETIMEDOUT) recorded by a device-side
+    wait of the last mslice_forward_static call on the current device."""
+    return int(_load().mslice_forward_static_status(_stream(stream)))
 
 
 def mslice_adjoint(p, vol, probe, g_psi, grad_vol, ws, stream=None):

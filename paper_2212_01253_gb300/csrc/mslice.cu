@@ -10,6 +10,8 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <mutex>
+
 #include <nvtx3/nvToolsExt.h>
 
 #include "mslice.h"
@@ -629,10 +631,28 @@ int run_gradient(const mslice_params* p, Plan& P, bool loss, cudaStream_t st) {
 // Allocation-free forward: the workspace is a fixed file-scope device array.
 // Host code must not use g_static_ws directly (its host-side name is a stand-in,
 // not a device address); its device address is taken once per device with
-// cudaGetSymbolAddress and cached.
+// cudaGetSymbolAddress, with that device current, and cached.  The cache is
+// guarded by a mutex, so first calls from several host threads are safe.
 constexpr size_t kStaticWsBytes = (size_t)32 << 20;
+constexpr int kStaticMaxDevices = 64;
 __device__ __align__(256) unsigned char g_static_ws[kStaticWsBytes];
-void* g_static_ws_ptr[64];
+void* g_static_ws_ptr[kStaticMaxDevices];
+std::mutex g_static_mu;
+
+// device address of g_static_ws on the current device (set-up on first use)
+int static_workspace(void** out) {
+    int dev = 0;
+    if (note(cudaGetDevice(&dev), "cudaGetDevice")) return MSLICE_ELAUNCH;
+    if (dev < 0 || dev >= kStaticMaxDevices) return MSLICE_EUNSUPPORTED;
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_ws_ptr[dev]) {
+        void* ptr = nullptr;
+        if (note(cudaGetSymbolAddress(&ptr, g_static_ws), "cudaGetSymbolAddress")) return MSLICE_ELAUNCH;
+        g_static_ws_ptr[dev] = ptr;
+    }
+    *out = g_static_ws_ptr[dev];
+    return MSLICE_OK;
+}
 
 }  // namespace
 
@@ -674,15 +694,16 @@ int mslice_forward_static(const mslice_params* p, const float* vol, const float*
     int rc = validate(p);
     if (rc) return rc;
     if (make_layout(p, MSLICE_OP_FORWARD).total > kStaticWsBytes) return MSLICE_EWORKSPACE;
-    int dev = 0;
-    if (note(cudaGetDevice(&dev), "cudaGetDevice")) return MSLICE_ELAUNCH;
-    if (dev < 0 || dev >= 64) return MSLICE_EUNSUPPORTED;
-    if (!g_static_ws_ptr[dev]) {
-        void* ptr = nullptr;
-        if (note(cudaGetSymbolAddress(&ptr, g_static_ws), "cudaGetSymbolAddress")) return MSLICE_ELAUNCH;
-        g_static_ws_ptr[dev] = ptr;
-    }
-    return mslice_forward(p, vol, probe, intensity, field_out, g_static_ws_ptr[dev], kStaticWsBytes, stream);
+    void* ws = nullptr;
+    if ((rc = static_workspace(&ws))) return rc;
+    return mslice_forward(p, vol, probe, intensity, field_out, ws, kStaticWsBytes, stream);
+}
+
+int mslice_forward_static_status(void* stream) {
+    void* ws = nullptr;
+    const int rc = static_workspace(&ws);
+    if (rc) return rc;
+    return mslice_status(ws, stream);
 }
 
 int mslice_adjoint(const mslice_params* p, const float* vol, const float* probe, const float* g_psi,

@@ -44,6 +44,8 @@ def test_static_forward_matches_workspace_forward_twice():
             torch.cuda.synchronize()
             err = float(torch.linalg.norm(out - ref) / torch.linalg.norm(ref))
             assert err <= TOL_I, err
+            # the status word of the library-owned workspace: no wait ran out
+            assert B.mslice_forward_static_status() == 0
 
 
 def test_static_forward_refuses_oversized_problems():

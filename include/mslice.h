@@ -120,10 +120,13 @@ typedef struct mslice_params {
                                   (capped at the co-resident maximum) */
     int32_t col_width;         /* launch shape: columns per column-pass group (4, 8 or 16),
                                   0 = automatic; see mslice_autotune in the Python package */
-    int32_t schedule;          /* slice-loop schedule: 0 = automatic (= 1), 1 = one grid barrier
+    int32_t schedule;          /* schedule of the angular-spectrum slice loop (MSLICE_ANGULAR, two
+                                  passes per slice): 0 = automatic (= 1), 1 = one grid barrier
                                   after each pass, 2 = the wavefields in two groups whose passes
                                   alternate with split-phase barriers (nw >= 2; results are
-                                  bitwise identical to 1; the autotuner tries both) */
+                                  bitwise identical to 1).  The paraxial slice loop runs one
+                                  pass per slice, alternating between rows and columns, with one
+                                  grid barrier per slice, and ignores this field. */
 } mslice_params;
 
 /* Bytes of workspace needed by `op` (MSLICE_OP_*) for these parameters;

@@ -2,10 +2,11 @@
 
 For a grid shape (ny, nz) and a number of wavefields nw it times the forward
 slice loop over a short synthetic volume for every candidate launch shape --
-the number of persistent blocks, the column-group width of the column pass
-(the number of adjacent columns whose z-FFTs one group of threads runs
-together) and, for nw >= 2, the slice-loop schedule (one grid barrier per pass,
-or two wavefield groups with split-phase barriers) -- and keeps the fastest.  Results are cached per device in a JSON
+the number of persistent blocks and the column-group width of the column
+passes (the number of adjacent columns whose z-FFTs one group of threads runs
+together) -- and keeps the fastest.  The paraxial slice loop runs one pass per
+slice with one grid barrier, so the split-phase schedule (an option of the
+angular-spectrum kernels) is not a candidate.  Results are cached per device in a JSON
 file next to the built library.  The shape changes only which threads do which
 transform, never the arithmetic, so results are bitwise independent of it.
 """
@@ -63,8 +64,7 @@ def col_widths(nz):
 
 def candidates(ny, nz, nw, sms):
     grids = sorted({0, sms, max(1, sms // 2), max(1, sms // 4)})
-    scheds = (1, 2) if nw >= 2 else (1,)
-    return [(g, cw, sc) for g in grids for cw in col_widths(nz) for sc in scheds]
+    return [(g, cw, 1) for g in grids for cw in col_widths(nz)]
 
 
 def _time_forward(ny, nz, nw, grid, cw, sched, ns=16, reps=3, device="cuda"):
@@ -92,7 +92,7 @@ def _time_forward(ny, nz, nw, grid, cw, sched, ns=16, reps=3, device="cuda"):
 def tune(ny, nz, nw, device="cuda", force=False):
     """(grid_blocks, col_width, schedule) for this shape, tuned on first use and cached."""
     dev = torch.device(device)
-    key = "v2|%s|%d|%d|%d" % (torch.cuda.get_device_name(dev), ny, nz, nw)
+    key = "v3|%s|%d|%d|%d" % (torch.cuda.get_device_name(dev), ny, nz, nw)
     with _lock:
         cache = _load_cache()
         if not force and key in cache:

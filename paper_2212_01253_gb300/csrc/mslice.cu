@@ -15,7 +15,7 @@
 #include <nvtx3/nvToolsExt.h>
 
 #include "mslice.h"
-#include "mslice_device.cuh"
+#include "mslice_slice.cuh"
 #include "mslice_kernels.h"
 
 namespace {
@@ -251,8 +251,9 @@ Layout make_layout(const mslice_params* p, int op) {
     }
     if (op == MSLICE_OP_ADJOINT || op == MSLICE_OP_LOSS_GRAD) {
         L.gfield = off; off = align256(off + fb);
-        L.gpart = off; off = align256(off + (p->nw > 1 && !(p->flags & MSLICE_PER_STRUCTURE)
-                                                  ? (p->schedule == 2 ? 2 : 1) * fb : 0));
+        // per-wavefield gradient partials, double-buffered by slice parity
+        // (one-pass loop, and the split-phase schedule of the two-pass loop)
+        L.gpart = off; off = align256(off + (p->nw > 1 && !(p->flags & MSLICE_PER_STRUCTURE) ? 2 * fb : 0));
         L.ckpt = off; off = align256(off + (size_t)L.nseg * fb);
         L.seg = off; off = align256(off + (size_t)L.K * fb);
     }
@@ -261,7 +262,8 @@ Layout make_layout(const mslice_params* p, int op) {
 }
 
 size_t smem_bytes(int ny, int nz, int cw) {
-    const size_t tabs = 2 * (size_t)(ny + nz) * sizeof(float2);
+    // tables, with room for the second propagator of the one-pass last slice
+    const size_t tabs = 3 * (size_t)(ny + nz) * sizeof(float2);
     size_t row = 0, col = 0;
     if (ny > 32) row = (size_t)(MS_THREADS / (ny / 32)) * (ny + ny / 32) * sizeof(float2);
     if (nz > 32) {
@@ -571,7 +573,7 @@ int prepare(const mslice_params* p, int op, const float* vol, const float* probe
         h.field = (float2*)(w + L.probe_half);
         h.j_begin = 0; h.j_end = 1;
         h.prop_last = 1;
-        h.flags = 0;
+        h.flags = P->ks.one_pass ? F_PROP_FULL : 0;   // both axes' factors
         rc = launch_coop(P->ks.fwd, P->grid, P->smem, h, st, KID_FWD, (double)p->nw * p->ny * p->nz);
         if (rc) return rc;
         a.probe = (const float2*)(w + L.probe_half);
@@ -601,7 +603,8 @@ int run_gradient(const mslice_params* p, Plan& P, bool loss, cudaStream_t st) {
         }
         a.j_end = p->ns;
         if ((rc = launch_coop(P.ks.last_loss, P.grid, P.smem, a, st, KID_LAST, u))) return rc;
-        if ((rc = launch_coop(P.ks.adj_start, P.grid, P.smem, a, st, KID_ADJ_START, 0.0)))
+        // two-pass loop: F_y^H of the seed; the one-pass adjoint's first pass does it
+        if (!P.ks.one_pass && (rc = launch_coop(P.ks.adj_start, P.grid, P.smem, a, st, KID_ADJ_START, 0.0)))
             return rc;
     } else {
         a.j_end = p->ns;
@@ -623,6 +626,7 @@ int run_gradient(const mslice_params* p, Plan& P, bool loss, cudaStream_t st) {
         SweepArgs b = P.base;
         b.j_begin = j0; b.j_end = j1;
         b.seg_base = j0;
+        if (P.ks.one_pass) b.flags = F_FIRST_FAR;   // slice ns-1 starts with F^H
         if ((rc = launch_coop(P.ks.adj, P.grid, P.smem, b, st, KID_ADJ, u * (j1 - j0)))) return rc;
     }
     return MSLICE_OK;
@@ -683,7 +687,12 @@ int mslice_forward(const mslice_params* p, const float* vol, const float* probe,
     }
     a.j_end = p->ns;
     if (p->flags & MSLICE_EXIT_WAVE) {
-        if (P.tab_half) a.tab = P.tab_half;   // the last propagation is a half step
+        // the last propagation is a half step (one-pass: only the factors after
+        // the last transmission; slice ns-2's second factor is a full step)
+        if (P.tab_half) {
+            if (P.ks.one_pass) a.tab2 = P.tab_half;
+            else a.tab = P.tab_half;
+        }
         return launch_coop(P.ks.last_exit, P.grid, P.smem, a, st, KID_LAST, u);
     }
     return launch_coop(P.ks.last_far, P.grid, P.smem, a, st, KID_LAST, u);

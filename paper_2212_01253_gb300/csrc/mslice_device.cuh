@@ -473,6 +473,8 @@ struct SweepArgs {
     int split;              // 1: two wavefield groups with split-phase barriers
     int exact;              // 1: exact 1 - n^2 transmission (gradient factor 1 - conj(v))
     const float2* p2d;      // [nz][ny] angular-spectrum propagator / (ny nz) (AS kernels only)
+    const float2* tab2;     // one-pass kernels: table whose P parts serve the last slice's
+                            // post-transmission propagation (half steps), or null
     float scales[MSLICE_MAX_ANGLES];  // per-wavefield loss scale when per_w
 };
 

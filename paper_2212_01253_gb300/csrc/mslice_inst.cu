@@ -1,6 +1,7 @@
-// mslice_inst.cu -- instances of the slice-loop kernels for one compile-time
-// row length MS_NY (set with -DMS_NY=...) and every column length 64..1024.
-#include "mslice_device.cuh"
+// mslice_inst.cu -- instances of the one-pass slice-loop kernels for one
+// compile-time row length MS_NY (set with -DMS_NY=...) and every column length
+// 64..1024.
+#include "mslice_slice.cuh"
 #include "mslice_kernels.h"
 
 #ifndef MS_NY
@@ -12,11 +13,11 @@
 
 ms_kernel_pair MS_CAT(ms_sweep_kernels_ny, MS_NY)(int nz) {
     switch (nz) {
-        case 64: return {(const void*)k_fwd_t<MS_NY, 64>, (const void*)k_adj_t<MS_NY, 64>};
-        case 128: return {(const void*)k_fwd_t<MS_NY, 128>, (const void*)k_adj_t<MS_NY, 128>};
-        case 256: return {(const void*)k_fwd_t<MS_NY, 256>, (const void*)k_adj_t<MS_NY, 256>};
-        case 512: return {(const void*)k_fwd_t<MS_NY, 512>, (const void*)k_adj_t<MS_NY, 512>};
-        case 1024: return {(const void*)k_fwd_t<MS_NY, 1024>, (const void*)k_adj_t<MS_NY, 1024>};
+        case 64: return {(const void*)k_slice_fwd<MS_NY, 64>, (const void*)k_slice_adj<MS_NY, 64>};
+        case 128: return {(const void*)k_slice_fwd<MS_NY, 128>, (const void*)k_slice_adj<MS_NY, 128>};
+        case 256: return {(const void*)k_slice_fwd<MS_NY, 256>, (const void*)k_slice_adj<MS_NY, 256>};
+        case 512: return {(const void*)k_slice_fwd<MS_NY, 512>, (const void*)k_slice_adj<MS_NY, 512>};
+        case 1024: return {(const void*)k_slice_fwd<MS_NY, 1024>, (const void*)k_slice_adj<MS_NY, 1024>};
         default: return {nullptr, nullptr};
     }
 }

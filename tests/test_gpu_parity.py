@@ -376,10 +376,11 @@ def test_checkpoint_interval_does_not_change_the_gradient():
 @pytest.mark.parametrize("ny,nz,ns,nw,K", [(64, 64, 24, 2, 5), (128, 64, 17, 3, 4), (512, 512, 40, 9, 32),
                                            (32, 32, 9, 5, 2)])
 def test_split_phase_schedule_is_bitwise_identical(ny, nz, ns, nw, K):
-    """Schedule 2 (two wavefield groups, split-phase barriers) reorders only
-    which blocks run which rows and columns when: every value is computed by
-    the same arithmetic, so intensities, loss and gradient equal schedule 1's."""
-    geo = oracle.Geometry(ny, nz, ns, alpha_i_deg=np.linspace(0.1, 0.5, nw))
+    """Schedule 2 of the angular-spectrum slice loop (two wavefield groups,
+    split-phase barriers) reorders only which blocks run which rows and columns
+    when: every value is computed by the same arithmetic, so intensities, loss
+    and gradient equal schedule 1's.  (The paraxial loop ignores the field.)"""
+    geo = oracle.Geometry(ny, nz, ns, alpha_i_deg=np.linspace(0.1, 0.5, nw), angular=True)
     vol = ci.random_volume(ny + ns + nw, ny, nz, ns, scale=40)
     I1 = G.forward(geo, vol, schedule=1)
     I2 = G.forward(geo, vol, schedule=2)

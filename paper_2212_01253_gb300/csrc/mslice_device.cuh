@@ -512,7 +512,7 @@ enum : int {
 };
 
 #ifndef MS_ADJ_CHUNK
-#define MS_ADJ_CHUNK 16  // a_j values loaded ahead of their gradient stores
+#define MS_ADJ_CHUNK 32  // a_j values loaded ahead of their gradient stores (all of a thread's)
 #endif
 
 // ----- row pass: one team of T = ny/32 threads (1 thread for ny <= 32) per row

@@ -220,70 +220,93 @@ __device__ void pass(const SweepArgs& A, const Smem2& S, double* s_red, const in
 #pragma unroll
                 for (int m = 0; m < 32; ++m) if (m < P) x[m] = __ldcg(A.gfield + fo + m * es);
             }
-            if ((A.flags & F_FIRST_FAR) && j == A.ns - 1) {   // uniform
-                fft<true>(x, N, T, t, reg, W, sync);
+            // U^H g_b t U^H as one rolled loop of four transforms; the pass of
+            // slice ns-1 starts with F^H = conj F conj / sqrt(N) instead
+            const bool far = (A.flags & F_FIRST_FAR) && j == A.ns - 1;   // uniform
+            if (far) {
 #pragma unroll
-                for (int m = 0; m < 32; ++m) x[m] = cscale(x[m], ff);
-            } else {
-                propagate<true>(x, N, T, t, reg, W, S.P[AX], sync);
+                for (int m = 0; m < 32; ++m) x[m].y = -x[m].y;
             }
-            if (active) {
-                // x = g_{a_j}: gradient -i kd a_j conj(g) (linearised) or with the
-                // factor (1 - conj(v)) (exact); the loads of a chunk of a_j are
-                // issued before the chunk's stores
-                const float2* a = A.seg + (size_t)(j - A.seg_base) * nw * npx + fo;
-                float2* gdst = (nw == 1 || A.per_w) ? (A.grad + vo)
-                                                    : (A.gpart + (size_t)(j & 1) * nw * npx + fo);
-                if (!A.exact) {
+#pragma unroll 1
+            for (int s = far ? 1 : 0; s < 4; ++s) {
+                fft<false>(x, N, T, t, reg, W, sync);
+                if (!(s & 1)) {
+                    const float2* Pt = S.P[AX];
 #pragma unroll
-                    for (int c0 = 0; c0 < 32; c0 += MS_ADJ_CHUNK) {
-                        float2 av[MS_ADJ_CHUNK];
-#pragma unroll
-                        for (int k = 0; k < MS_ADJ_CHUNK; ++k)
-                            if (c0 + k < P) av[k] = __ldcg(a + (c0 + k) * es);
-#pragma unroll
-                        for (int k = 0; k < MS_ADJ_CHUNK; ++k) {
-                            if (c0 + k < P) {
-                                const float2 g = x[c0 + k];
-                                const float re = fmaf(av[k].x, g.x, av[k].y * g.y);   // Re(a conj g)
-                                const float im = fmaf(av[k].y, g.x, -av[k].x * g.y);  // Im(a conj g)
-                                __stcg(gdst + (c0 + k) * es, make_float2(A.kd * im, -A.kd * re));
-                            }
+                    for (int m = 0; m < 32; ++m) {
+                        if (m < P) {
+                            const float2 p = Pt[t + T * m], X = x[m];
+                            x[m] = make_float2(fmaf(X.x, p.x, X.y * p.y), fmaf(X.x, p.y, -X.y * p.x));
                         }
                     }
                 } else {
-                    const float2* vv = A.vol + vo;
 #pragma unroll
-                    for (int c0 = 0; c0 < 32; c0 += 8) {
-                        float2 av[8], vk[8];
+                    for (int m = 0; m < 32; ++m) x[m].y = -x[m].y;
+                    if (s == 1) {
+                        if (far) {
 #pragma unroll
-                        for (int k = 0; k < 8; ++k) {
-                            if (c0 + k < P) {
-                                av[k] = __ldcg(a + (c0 + k) * es);
-                                vk[k] = __ldg(vv + (c0 + k) * es);
+                            for (int m = 0; m < 32; ++m) x[m] = cscale(x[m], ff);
+                        }
+                        if (active) {
+                            // x = g_{a_j}: gradient -i kd a_j conj(g) (linearised) or with the
+                            // factor (1 - conj(v)) (exact); the loads of a chunk of a_j are
+                            // issued before the chunk's stores
+                            const float2* a = A.seg + (size_t)(j - A.seg_base) * nw * npx + fo;
+                            float2* gdst = (nw == 1 || A.per_w) ? (A.grad + vo)
+                                                                : (A.gpart + (size_t)(j & 1) * nw * npx + fo);
+                            if (!A.exact) {
+#pragma unroll
+                                for (int c0 = 0; c0 < 32; c0 += MS_ADJ_CHUNK) {
+                                    float2 av[MS_ADJ_CHUNK];
+#pragma unroll
+                                    for (int k = 0; k < MS_ADJ_CHUNK; ++k)
+                                        if (c0 + k < P) av[k] = __ldcg(a + (c0 + k) * es);
+#pragma unroll
+                                    for (int k = 0; k < MS_ADJ_CHUNK; ++k) {
+                                        if (c0 + k < P) {
+                                            const float2 g = x[c0 + k];
+                                            const float re = fmaf(av[k].x, g.x, av[k].y * g.y);   // Re(a conj g)
+                                            const float im = fmaf(av[k].y, g.x, -av[k].x * g.y);  // Im(a conj g)
+                                            __stcg(gdst + (c0 + k) * es, make_float2(A.kd * im, -A.kd * re));
+                                        }
+                                    }
+                                }
+                            } else {
+                                const float2* vv = A.vol + vo;
+#pragma unroll
+                                for (int c0 = 0; c0 < 32; c0 += 8) {
+                                    float2 av[8], vk[8];
+#pragma unroll
+                                    for (int k = 0; k < 8; ++k) {
+                                        if (c0 + k < P) {
+                                            av[k] = __ldcg(a + (c0 + k) * es);
+                                            vk[k] = __ldg(vv + (c0 + k) * es);
+                                        }
+                                    }
+#pragma unroll
+                                    for (int k = 0; k < 8; ++k) {
+                                        if (c0 + k < P) {
+                                            const float2 g = x[c0 + k];
+                                            const float re = fmaf(av[k].x, g.x, av[k].y * g.y);
+                                            const float im = fmaf(av[k].y, g.x, -av[k].x * g.y);
+                                            const float fr = 1.f - vk[k].x, fi = vk[k].y;       // 1 - conj(v)
+                                            const float cr = fmaf(fr, re, -fi * im), ci = fmaf(fr, im, fi * re);
+                                            __stcg(gdst + (c0 + k) * es, make_float2(A.kd * ci, -A.kd * cr));
+                                        }
+                                    }
+                                }
+                            }
+                            if (prop) {
+                                const float2* tv = A.tvol + vo;
+#pragma unroll
+                                for (int m = 0; m < 32; ++m) if (m < P) x[m] = cmulc_t(x[m], __ldg(tv + m * es));
                             }
                         }
-#pragma unroll
-                        for (int k = 0; k < 8; ++k) {
-                            if (c0 + k < P) {
-                                const float2 g = x[c0 + k];
-                                const float re = fmaf(av[k].x, g.x, av[k].y * g.y);
-                                const float im = fmaf(av[k].y, g.x, -av[k].x * g.y);
-                                const float fr = 1.f - vk[k].x, fi = vk[k].y;       // 1 - conj(v)
-                                const float cr = fmaf(fr, re, -fi * im), ci = fmaf(fr, im, fi * re);
-                                __stcg(gdst + (c0 + k) * es, make_float2(A.kd * ci, -A.kd * cr));
-                            }
-                        }
+                        if (!prop) break;   // uniform
                     }
-                }
-                if (prop) {
-                    const float2* tv = A.tvol + vo;
-#pragma unroll
-                    for (int m = 0; m < 32; ++m) if (m < P) x[m] = cmulc_t(x[m], __ldg(tv + m * es));
                 }
             }
             if (!prop) continue;   // uniform
-            propagate<true>(x, N, T, t, reg, W, S.P[AX], sync);
             if (active) {
 #pragma unroll
                 for (int m = 0; m < 32; ++m) if (m < P) __stcg(A.gfield + fo + m * es, x[m]);
@@ -468,13 +491,11 @@ __global__ void __launch_bounds__(MS_THREADS, MS_MIN_BLOCKS) k_slice_fwd(const S
 template <int NY, int NZ>
 __global__ void __launch_bounds__(MS_THREADS, MS_MIN_BLOCKS) k_slice_adj(const SweepArgs A) {
     MS_KERNEL_PROLOGUE2
-    const size_t npx = (size_t)A.ny * A.nz;
     const bool reduce = A.nw > 1 && !A.per_w;
     for (int j = A.j_end - 1; j >= A.j_begin; --j) {
-        if (j - 1 >= A.j_begin) {
-            prefetch_slice(A, A.tvol, j - 1);
-            prefetch_l2(A.seg + (size_t)(j - 1 - A.seg_base) * A.nw * npx, A.nw * npx * sizeof(float2));
-        }
+        // the next slice's transmission into L2 (a_j is not prefetched: one
+        // slice of it for every wavefield would evict the fields and partials)
+        if (j - 1 >= A.j_begin) prefetch_slice(A, A.tvol, j - 1);
         pass_j<P_ADJ, NY, NZ>(A, S, s_red, j, false, j > 0);
         if (reduce || j > A.j_begin) {
             if (!grid.sync()) return;

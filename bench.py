@@ -490,7 +490,9 @@ def run_batch(args):
             "dtype": "f32", "data": "synthetic",
             "config": {"workload": "%d structures, grids 128-512 per axis, 128-1024 slices, 0.1-0.5 deg, "
                                    "one CUDA graph per rank" % len(all_specs),
-                       "structures_rank0": len(jobs), "groups_rank0": len(bat.groups), "lanes": len(bat.lanes),
+                       "structures_rank0": len(jobs), "groups_rank0": bat.ngroups, "lanes": bat.lanes,
+                       "api": "mslice_loss_grad_batched (one C call: grouping, lanes and launch sequences "
+                              "in the library)",
                        "units_per_step_rank0": bat.units, "setup_s": setup_s}}
     print(json.dumps(line), flush=True)
     if world > 1:

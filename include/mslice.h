@@ -203,6 +203,74 @@ int mslice_loss_grad_multi(const mslice_params *p, const float *vols, const floa
                            float *grad_vol, float *intensity, void *ws, size_t ws_bytes,
                            void *stream);
 
+/* ------------------------------------------------------------------------
+ * Batched runs of many independent structures of uneven grid shape (the
+ * paper's forward model of Eq. 1 and the loss of Eq. 4, for many samples at
+ * once; the batching itself has no counterpart in the paper).  Jobs of one
+ * grid shape (ny, nz, ns) advance together as the wavefields of one
+ * per-structure run (up to MSLICE_MAX_ANGLES per run); the runs ("groups") are
+ * spread over `lanes` library-owned streams (longest first onto the least
+ * loaded lane, the persistent kernels of each on SMs / lanes blocks so that
+ * concurrent runs fit on the GPU together), forked from and joined back into
+ * `stream`.  Every job's results are bitwise those of a single-structure call
+ * with the same launch shape.
+ * ------------------------------------------------------------------------ */
+typedef struct mslice_job {
+    int32_t ny, nz, ns;        /* grid of this structure: powers of two in [1, MSLICE_MAX_N], ns >= 1 */
+    int32_t col_width;         /* launch shape of this job's group (the group takes its first job's):
+                                  columns per column-pass group, 0 = automatic */
+    double alpha_i_rad;        /* incidence angle */
+    float scale;               /* s > 0: model intensity scale of the loss (loss + gradient only) */
+    float reserved;            /* 0 */
+    const float *vol;          /* [ns][nz][ny] complex delta + i beta, device, 16-byte aligned */
+    const float *meas_amp;     /* [nz][ny] float sqrt(I_meas), device (loss + gradient only) */
+    float *grad_vol;           /* [ns][nz][ny] complex out: dL/ddelta + i dL/dbeta (loss + gradient) */
+    float *intensity;          /* [nz][ny] float out: I (required by the forward; may be NULL otherwise) */
+    double *loss_out;          /* device double[1] out: this job's loss, or NULL (loss + gradient) */
+} mslice_job;
+
+/* Bytes of workspace of a batched call (op MSLICE_OP_FORWARD or
+ * MSLICE_OP_LOSS_GRAD) for these jobs and lanes; 0 if the request is invalid.
+ * `common` gives the wavelength, slice thickness, pixel sizes, in-plane angle,
+ * checkpoint interval, flags (MSLICE_EXACT_TRANSMISSION, MSLICE_STRANG;
+ * MSLICE_EXIT_WAVE for the forward) and grid_blocks (used when lanes == 1);
+ * its ny, nz, ns, nw and alpha_i_rad are ignored. */
+size_t mslice_batched_workspace_size(const mslice_params *common, const mslice_job *jobs, int njobs, int op,
+                                     int lanes);
+
+/* Loss and gradient of every job: jobs[i].grad_vol, jobs[i].loss_out (if
+ * given) and jobs[i].intensity (if given); loss_total: NULL or device
+ * double[1], the sum of the jobs' losses (FP64, summed per group in job order
+ * and over the groups in order).  1 <= lanes <= 16.  The lane streams and
+ * events are created on the first call with lanes > 1 on a device: make that
+ * call before any stream capture.  Calls that share the workspace, or that
+ * run with lanes > 1 at the same time on one device, must not overlap.
+ * Errors: MSLICE_EINVAL (a bad job, pointer, alignment or lane count),
+ * MSLICE_EUNSUPPORTED (MSLICE_ANGULAR, or MSLICE_EXIT_WAVE), MSLICE_EWORKSPACE,
+ * MSLICE_ELAUNCH. */
+int mslice_loss_grad_batched(const mslice_params *common, const mslice_job *jobs, int njobs, int lanes,
+                             double *loss_total, void *ws, size_t ws_bytes, void *stream);
+
+/* The plan of a batched call, on the host (no device work): *ngroups, and
+ * for every job its group (group_of_job[njobs], may be NULL), for every group
+ * its lane (lane_of_group[ngroups], may be NULL; at most njobs groups).
+ * Groups are numbered in order of their first job; a group holds the jobs of
+ * one grid shape (ny, nz, ns), at most MSLICE_MAX_ANGLES, in job order. */
+int mslice_batched_plan(const mslice_params *common, const mslice_job *jobs, int njobs, int op, int lanes,
+                        int *group_of_job, int *lane_of_group, int *ngroups);
+
+/* mslice_status() of every group of a batched call (same jobs, op and lanes):
+ * waits for `stream`, then MSLICE_OK, or MSLICE_ETIMEDOUT if a bounded
+ * device-side wait of any group ran out. */
+int mslice_batched_status(const mslice_params *common, const mslice_job *jobs, int njobs, int op, int lanes,
+                          const void *ws, void *stream);
+
+/* Far-field intensity of every job into jobs[i].intensity (the exit wave's
+ * with MSLICE_EXIT_WAVE).  Arguments and errors as for
+ * mslice_loss_grad_batched. */
+int mslice_forward_batched(const mslice_params *common, const mslice_job *jobs, int njobs, int lanes, void *ws,
+                           size_t ws_bytes, void *stream);
+
 /* The FP64-built constant arrays ("C" of Fig. 1), rounded to float:
  *   py [ny] complex: exp(-i Delta k_y^2 / 2k);  pz [nz] complex: exp(-i Delta k_z^2 / 2k)
  *   probe_z [nw][nz] complex: exp(-i k sin(alpha_w) z_l) (default probe, one value per row)

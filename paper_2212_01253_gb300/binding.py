@@ -98,6 +98,34 @@ def make_coarse(shape, block, offset=(0, 0, 0), beta_ratio=4.9e-6 / 4.7e-5, base
     return c
 
 
+class mslice_job(ctypes.Structure):
+    _fields_ = [("ny", ctypes.c_int32), ("nz", ctypes.c_int32), ("ns", ctypes.c_int32),
+                ("col_width", ctypes.c_int32), ("alpha_i_rad", ctypes.c_double), ("scale", ctypes.c_float),
+                ("reserved", ctypes.c_float), ("vol", ctypes.c_void_p), ("meas_amp", ctypes.c_void_p),
+                ("grad_vol", ctypes.c_void_p), ("intensity", ctypes.c_void_p), ("loss_out", ctypes.c_void_p)]
+
+
+def make_jobs(jobs):
+    """A ctypes array of mslice_job from dicts with 'vol' (complex64 [ns][nz][ny]),
+    'alpha_deg' and optionally 'meas' (float32 [nz][ny]), 'scale', 'grad'
+    (complex64 like vol), 'intensity' (float32 [nz][ny]), 'loss' (float64 [1]),
+    'col_width' -- CUDA tensors, kept alive by the caller."""
+    arr = (mslice_job * len(jobs))()
+    for i, jb in enumerate(jobs):
+        ns, nz, ny = jb["vol"].shape
+        j = arr[i]
+        j.ny, j.nz, j.ns = int(ny), int(nz), int(ns)
+        j.col_width = int(jb.get("col_width", 0))
+        j.alpha_i_rad = math.radians(float(jb["alpha_deg"]))
+        j.scale = float(jb.get("scale", 1.0))
+        j.vol = _ptr(jb["vol"], torch.complex64, ns * nz * ny, "vol")
+        j.meas_amp = _ptr(jb.get("meas"), torch.float32, nz * ny, "meas")
+        j.grad_vol = _ptr(jb.get("grad"), torch.complex64, ns * nz * ny, "grad")
+        j.intensity = _ptr(jb.get("intensity"), torch.float32, nz * ny, "intensity")
+        j.loss_out = _ptr(jb.get("loss"), torch.float64, 1, "loss")
+    return arr
+
+
 class mslice_kernel_time(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int32),
                 ("total_ms", ctypes.c_double), ("units", ctypes.c_double)]
@@ -127,6 +155,12 @@ def _load():
                                      ctypes.c_int),
                 "mslice_plan_tables": ([P, vp, vp, vp, vp, sz, vp], ctypes.c_int),
                 "mslice_loss_grad_multi": ([P, vp, vp, vp, vp, vp, vp, vp, vp, sz, vp], ctypes.c_int),
+                "mslice_batched_workspace_size": ([P, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int], sz),
+                "mslice_loss_grad_batched": ([P, vp, ctypes.c_int, ctypes.c_int, vp, vp, sz, vp], ctypes.c_int),
+                "mslice_forward_batched": ([P, vp, ctypes.c_int, ctypes.c_int, vp, sz, vp], ctypes.c_int),
+                "mslice_batched_status": ([P, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp], ctypes.c_int),
+                "mslice_batched_plan": ([P, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp, vp],
+                                        ctypes.c_int),
                 "mslice_transmission": ([P, vp, vp, vp], ctypes.c_int),
                 "mslice_status": ([vp, vp], ctypes.c_int),
                 "mslice_intensity_vjp": ([vp, vp, vp, sz, vp], ctypes.c_int),
@@ -268,6 +302,44 @@ def mslice_loss_grad(p, vol, probe, meas_amp, scale, loss_out, grad_vol, intensi
         _ptr(grad_vol, torch.complex64, nvol, "grad_vol"),
         _ptr(intensity, torch.float32, nfield, "intensity"),
         _ptr(ws, torch.uint8, None, "ws"), ws.numel(), _stream(stream)), "mslice_loss_grad")
+
+
+def mslice_batched_workspace_size(common, jobs, op, lanes=1) -> int:
+    """jobs: the ctypes array of make_jobs()."""
+    n = _load().mslice_batched_workspace_size(ctypes.byref(common), ctypes.cast(jobs, ctypes.c_void_p), len(jobs),
+                                              int(op), int(lanes))
+    if n == 0:
+        raise MsliceError(-1, "mslice_batched_workspace_size")
+    return int(n)
+
+
+def mslice_loss_grad_batched(common, jobs, lanes, loss_total, ws, stream=None):
+    _check(_load().mslice_loss_grad_batched(
+        ctypes.byref(common), ctypes.cast(jobs, ctypes.c_void_p), len(jobs), int(lanes),
+        _ptr(loss_total, torch.float64, 1, "loss_total"), _ptr(ws, torch.uint8, None, "ws"), ws.numel(),
+        _stream(stream)), "mslice_loss_grad_batched")
+
+
+def mslice_forward_batched(common, jobs, lanes, ws, stream=None):
+    _check(_load().mslice_forward_batched(
+        ctypes.byref(common), ctypes.cast(jobs, ctypes.c_void_p), len(jobs), int(lanes),
+        _ptr(ws, torch.uint8, None, "ws"), ws.numel(), _stream(stream)), "mslice_forward_batched")
+
+
+def mslice_batched_plan(common, jobs, op, lanes=1):
+    """(group of each job, lane of each group) of a batched call (host only)."""
+    n = len(jobs)
+    gj, lg, ng = (ctypes.c_int * n)(), (ctypes.c_int * n)(), ctypes.c_int(0)
+    _check(_load().mslice_batched_plan(ctypes.byref(common), ctypes.cast(jobs, ctypes.c_void_p), n, int(op),
+                                       int(lanes), ctypes.cast(gj, ctypes.c_void_p), ctypes.cast(lg, ctypes.c_void_p),
+                                       ctypes.byref(ng)), "mslice_batched_plan")
+    return list(gj), list(lg)[:ng.value]
+
+
+def mslice_batched_status(common, jobs, op, lanes, ws, stream=None) -> int:
+    return int(_load().mslice_batched_status(ctypes.byref(common), ctypes.cast(jobs, ctypes.c_void_p), len(jobs),
+                                             int(op), int(lanes), _ptr(ws, torch.uint8, None, "ws"),
+                                             _stream(stream)))
 
 
 def mslice_loss_grad_multi(p, vols, probe, meas_amp, scales, loss_out, grad_vol, intensity, ws, stream=None):

@@ -10,7 +10,9 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <mutex>
+#include <vector>
 
 #include <nvtx3/nvToolsExt.h>
 
@@ -221,6 +223,7 @@ struct Layout {
     size_t ctrl, partials, tab, probe_z, probe_y, tvol, field, gfield, gpart, ckpt, seg;
     size_t tab_half, probe_half, zero_t;  // symmetric splitting only (0 otherwise)
     size_t p2d;                           // angular spectrum only (0 otherwise)
+    size_t loss_task, loss_wsum;          // one-pass loss partials (loss + gradient)
     size_t total;
     int K, nseg;
 };
@@ -256,6 +259,11 @@ Layout make_layout(const mslice_params* p, int op) {
         L.gpart = off; off = align256(off + (p->nw > 1 && !(p->flags & MSLICE_PER_STRUCTURE) ? 2 * fb : 0));
         L.ckpt = off; off = align256(off + (size_t)L.nseg * fb);
         L.seg = off; off = align256(off + (size_t)L.K * fb);
+        // one FP64 partial per task of the detector pass (<= nw max(ny, nz)
+        // tasks on either axis) and per-wavefield sums
+        const size_t nmax = (size_t)(p->ny > p->nz ? p->ny : p->nz);
+        L.loss_task = off; off = align256(off + (size_t)p->nw * nmax * sizeof(double));
+        L.loss_wsum = off; off = align256(off + (size_t)p->nw * sizeof(double));
     }
     L.total = off;
     return L;
@@ -466,6 +474,31 @@ int launch_transmission(const float2* vol, float2* tv, size_t nvox, double kd, i
     return MSLICE_OK;
 }
 
+// Buffers of each structure of a per-structure run (MSLICE_PER_STRUCTURE):
+// contiguous [nw][...] arrays of the caller, or the separate buffers of the
+// jobs of a batched call.
+struct JobTable {
+    const float2* vol[MSLICE_MAX_ANGLES];
+    float2* grad[MSLICE_MAX_ANGLES];
+    const float* meas[MSLICE_MAX_ANGLES];
+    float* inten[MSLICE_MAX_ANGLES];
+    double* loss[MSLICE_MAX_ANGLES];
+};
+
+// the table of contiguous [nw][ns][nz][ny] volumes / gradients and
+// [nw][nz][ny] amplitudes / intensities (any of them may be null)
+JobTable contiguous_table(const mslice_params* p, const float* vols, float* grads, const float* meas, float* inten) {
+    JobTable jt{};
+    const size_t npx = (size_t)p->ny * p->nz, nv = (size_t)p->ns * npx;
+    for (int w = 0; w < p->nw; ++w) {
+        jt.vol[w] = vols ? (const float2*)vols + w * nv : nullptr;
+        jt.grad[w] = grads ? (float2*)grads + w * nv : nullptr;
+        jt.meas[w] = meas ? meas + w * npx : nullptr;
+        jt.inten[w] = inten ? inten + w * npx : nullptr;
+    }
+    return jt;
+}
+
 struct Plan {
     KernelSet ks;
     Layout L;
@@ -476,11 +509,19 @@ struct Plan {
     const float2* tab_half;  // P over Delta/2 (symmetric splitting), else null
 };
 
+// jt: per-structure buffers (per-structure runs: the transmission of each
+// structure is computed from its own volume), else null
 int prepare(const mslice_params* p, int op, const float* vol, const float* probe, void* ws, size_t ws_bytes,
             cudaStream_t st, Plan* P, float2* py_out = nullptr, float2* pz_out = nullptr,
-            float2* probe_z_out = nullptr) {
+            float2* probe_z_out = nullptr, const JobTable* jt = nullptr) {
     int rc = validate(p);
     if (rc) return rc;
+    const bool per_w = (p->flags & MSLICE_PER_STRUCTURE) != 0;
+    if (per_w && jt) {
+        for (int w = 0; w < p->nw; ++w)
+            if (!jt->vol[w] || ((uintptr_t)jt->vol[w] & 15)) return MSLICE_EINVAL;
+        vol = (const float*)jt->vol[0];
+    }
     if (!vol || !ws || ((uintptr_t)ws & 255) || ((uintptr_t)vol & 15) || ((uintptr_t)probe & 7)) return MSLICE_EINVAL;
     P->L = make_layout(p, op);
     if (ws_bytes < P->L.total) return MSLICE_EWORKSPACE;
@@ -518,7 +559,13 @@ int prepare(const mslice_params* p, int op, const float* vol, const float* probe
     r = prof_begin(KID_TRANSMISSION, (double)nvox, st);
     const int exact = (p->flags & MSLICE_EXACT_TRANSMISSION) ? 1 : 0;
     // the workspace holds u = t - 1 (applied as a + a u by the slice loops)
-    rc = launch_transmission((const float2*)vol, (float2*)(w + L.tvol), nvox, kd, exact, 1, st);
+    if (per_w && jt) {
+        const size_t nv = (size_t)p->ns * p->ny * p->nz;
+        for (int q = 0; q < p->nw && !rc; ++q)
+            rc = launch_transmission(jt->vol[q], (float2*)(w + L.tvol) + q * nv, nv, kd, exact, 1, st);
+    } else {
+        rc = launch_transmission((const float2*)vol, (float2*)(w + L.tvol), nvox, kd, exact, 1, st);
+    }
     prof_end(r, st);
     if (rc) return rc;
     SweepArgs& a = P->base;
@@ -542,6 +589,19 @@ int prepare(const mslice_params* p, int op, const float* vol, const float* probe
         a.seg = (float2*)(w + L.seg);
     }
     a.partials = (double*)(w + L.partials);
+    if (op == MSLICE_OP_LOSS_GRAD) {
+        a.loss_task = (double*)(w + L.loss_task);
+        a.loss_wsum = (double*)(w + L.loss_wsum);
+    }
+    if (per_w && jt) {
+        for (int q = 0; q < p->nw; ++q) {
+            a.volw[q] = jt->vol[q];
+            a.gradw[q] = jt->grad[q];
+            a.measw[q] = jt->meas[q];
+            a.intw[q] = jt->inten[q];
+            a.lossw[q] = jt->loss[q];
+        }
+    }
     a.ctrl = (unsigned*)(w + L.ctrl);
     a.timeout_ns = kDefaultTimeoutNs;
     a.K = L.K;
@@ -632,6 +692,217 @@ int run_gradient(const mslice_params* p, Plan& P, bool loss, cudaStream_t st) {
     return MSLICE_OK;
 }
 
+// Forward launch sequence after prepare(): slice loop over [0, ns-1), then the
+// last slice with the far field (or the exit wave)
+int run_forward(const mslice_params* p, Plan& P, float* intensity, float* field_out, cudaStream_t st) {
+    int rc;
+    const double u = (double)p->nw * p->ny * p->nz;
+    SweepArgs a = P.base;
+    a.intensity = intensity;
+    a.field_out = (float2*)field_out;
+    a.j_begin = 0;
+    if (p->ns > 1) {
+        a.j_end = p->ns - 1;
+        a.prop_last = 1;
+        if ((rc = launch_coop(P.ks.fwd, P.grid, P.smem, a, st, KID_FWD, u * (p->ns - 1)))) return rc;
+    }
+    a.j_end = p->ns;
+    if (p->flags & MSLICE_EXIT_WAVE) {
+        // the last propagation is a half step (one-pass: only the factors after
+        // the last transmission; slice ns-2's second factor is a full step)
+        if (P.tab_half) {
+            if (P.ks.one_pass) a.tab2 = P.tab_half;
+            else a.tab = P.tab_half;
+        }
+        return launch_coop(P.ks.last_exit, P.grid, P.smem, a, st, KID_LAST, u);
+    }
+    return launch_coop(P.ks.last_far, P.grid, P.smem, a, st, KID_LAST, u);
+}
+
+// ---------------------------------------------------------------------------
+// batched runs of uneven structures (mslice_*_batched)
+// ---------------------------------------------------------------------------
+// sum of n doubles in index order (the batch's loss over its groups)
+__global__ void k_sum_doubles(const double* __restrict__ x, int n, double* out) {
+    double s = 0.0;
+    for (int i = 0; i < n; ++i) s += x[i];
+    *out = s;
+}
+
+// Jobs of one grid shape, advanced as the wavefields of one per-structure run
+// (at most MSLICE_MAX_ANGLES per group).
+struct Group {
+    int ny, nz, ns, n;
+    int idx[MSLICE_MAX_ANGLES];   // job indices, in job order
+    double cost;                  // modelled time (lane assignment)
+    size_t ws_off, ws_bytes;      // region of the batch workspace
+    int lane;
+};
+
+constexpr int kMaxLanes = 16;
+
+// parameters of a group's run: the common ones with the group's grid, angles
+// and launch shape
+mslice_params group_params(const mslice_params* common, const mslice_job* jobs, const Group& g, int op,
+                           int lanes, int sms) {
+    mslice_params q = *common;
+    q.ny = g.ny; q.nz = g.nz; q.ns = g.ns; q.nw = g.n;
+    for (int k = 0; k < g.n; ++k) q.alpha_i_rad[k] = jobs[g.idx[k]].alpha_i_rad;
+    q.flags |= MSLICE_PER_STRUCTURE;
+    const int cw = jobs[g.idx[0]].col_width;
+    if (cw > 0) q.col_width = cw;
+    if (lanes > 1) q.grid_blocks = sms / lanes > 0 ? sms / lanes : 1;
+    return q;
+}
+
+// Groups jobs by grid shape (in order of first appearance), assigns the groups
+// to lanes longest first onto the least loaded lane (ties: the lowest lane),
+// and lays out the batch workspace: ngroups FP64 loss totals, then one
+// workspace region per group.  Returns 0 or an error code.
+int plan_batch(const mslice_params* common, const mslice_job* jobs, int njobs, int op, int lanes,
+               std::vector<Group>& G, size_t* total, int sms) {
+    if (!common || !jobs || njobs < 1 || lanes < 1 || lanes > kMaxLanes) return MSLICE_EINVAL;
+    if (common->flags & MSLICE_ANGULAR) return MSLICE_EUNSUPPORTED;
+    if (op == MSLICE_OP_LOSS_GRAD && (common->flags & MSLICE_EXIT_WAVE)) return MSLICE_EUNSUPPORTED;
+    G.clear();
+    for (int i = 0; i < njobs; ++i) {
+        const mslice_job& jb = jobs[i];
+        if (!is_pow2(jb.ny) || !is_pow2(jb.nz) || jb.ny > MSLICE_MAX_N || jb.nz > MSLICE_MAX_N || jb.ns < 1)
+            return MSLICE_EINVAL;
+        if (!jb.vol || ((uintptr_t)jb.vol & 15)) return MSLICE_EINVAL;
+        if (op == MSLICE_OP_LOSS_GRAD && (!jb.meas_amp || !jb.grad_vol || !(jb.scale > 0.f))) return MSLICE_EINVAL;
+        if (op == MSLICE_OP_FORWARD && !jb.intensity) return MSLICE_EINVAL;
+        Group* g = nullptr;
+        for (auto& h : G)
+            if (h.ny == jb.ny && h.nz == jb.nz && h.ns == jb.ns && h.n < MSLICE_MAX_ANGLES) { g = &h; break; }
+        if (!g) {
+            G.push_back(Group{});
+            g = &G.back();
+            g->ny = jb.ny; g->nz = jb.nz; g->ns = jb.ns; g->n = 0;
+        }
+        g->idx[g->n++] = i;
+    }
+    size_t off = align256((size_t)G.size() * sizeof(double));
+    std::vector<double> load(lanes, 0.0);
+    std::vector<int> order(G.size());
+    for (size_t k = 0; k < G.size(); ++k) {
+        Group& g = G[k];
+        const mslice_params q = group_params(common, jobs, g, op, lanes, sms);
+        if (validate(&q)) return MSLICE_EINVAL;
+        g.ws_off = off;
+        g.ws_bytes = make_layout(&q, op).total;
+        off = align256(off + g.ws_bytes);
+        // work plus a per-slice latency term (grid barriers of latency-bound slice steps)
+        g.cost = (double)g.n * g.ny * g.nz * g.ns / 4e10 + g.ns * 2.5e-5;
+        order[k] = (int)k;
+    }
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return G[a].cost > G[b].cost; });
+    for (int k : order) {
+        int best = 0;
+        for (int l = 1; l < lanes; ++l)
+            if (load[l] < load[best]) best = l;
+        G[k].lane = best;
+        load[best] += G[k].cost;
+    }
+    *total = off;
+    return MSLICE_OK;
+}
+
+// library-owned streams and events of the lanes, per device (created on first use)
+struct LaneSet {
+    bool init = false;
+    cudaStream_t s[kMaxLanes];
+    cudaEvent_t fork, join[kMaxLanes];
+};
+LaneSet g_lane_sets[64];
+std::mutex g_lane_mu;
+
+int lane_set(LaneSet** out) {
+    int dev = 0;
+    if (note(cudaGetDevice(&dev), "cudaGetDevice") || dev < 0 || dev >= 64) return MSLICE_ELAUNCH;
+    std::lock_guard<std::mutex> lock(g_lane_mu);
+    LaneSet& L = g_lane_sets[dev];
+    if (!L.init) {
+        if (note(cudaEventCreateWithFlags(&L.fork, cudaEventDisableTiming), "cudaEventCreateWithFlags"))
+            return MSLICE_ELAUNCH;
+        for (int l = 0; l < kMaxLanes; ++l) {
+            if (note(cudaStreamCreateWithFlags(&L.s[l], cudaStreamNonBlocking), "cudaStreamCreateWithFlags") ||
+                note(cudaEventCreateWithFlags(&L.join[l], cudaEventDisableTiming), "cudaEventCreateWithFlags"))
+                return MSLICE_ELAUNCH;
+        }
+        L.init = true;
+    }
+    *out = &L;
+    return MSLICE_OK;
+}
+
+int run_batch(const mslice_params* common, const mslice_job* jobs, int njobs, int lanes, int op, double* loss_total,
+              void* ws, size_t ws_bytes, cudaStream_t st) {
+    if (!ws || ((uintptr_t)ws & 255)) return MSLICE_EINVAL;
+    int dev = 0, sms = 0;
+    if (note(cudaGetDevice(&dev), "cudaGetDevice") ||
+        note(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "cudaDeviceGetAttribute"))
+        return MSLICE_ELAUNCH;
+    std::vector<Group> G;
+    size_t total = 0;
+    int rc = plan_batch(common, jobs, njobs, op, lanes, G, &total, sms);
+    if (rc) return rc;
+    if (ws_bytes < total) return MSLICE_EWORKSPACE;
+    LaneSet* L = nullptr;
+    if (lanes > 1) {
+        if ((rc = lane_set(&L))) return rc;
+        if (note(cudaEventRecord(L->fork, st), "cudaEventRecord")) return MSLICE_ELAUNCH;
+        for (int l = 0; l < lanes; ++l)
+            if (note(cudaStreamWaitEvent(L->s[l], L->fork, 0), "cudaStreamWaitEvent")) return MSLICE_ELAUNCH;
+    }
+    double* totals = (double*)ws;
+    // every lane's groups in the order they were placed (longest first)
+    std::vector<int> order(G.size());
+    for (size_t k = 0; k < G.size(); ++k) order[k] = (int)k;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return G[a].cost > G[b].cost; });
+    for (int k : order) {
+        const Group& g = G[k];
+        const cudaStream_t gs = lanes > 1 ? L->s[g.lane] : st;
+        const mslice_params q = group_params(common, jobs, g, op, lanes, sms);
+        JobTable jt{};
+        float scales[MSLICE_MAX_ANGLES];
+        for (int w = 0; w < g.n; ++w) {
+            const mslice_job& jb = jobs[g.idx[w]];
+            jt.vol[w] = (const float2*)jb.vol;
+            jt.grad[w] = (float2*)jb.grad_vol;
+            jt.meas[w] = jb.meas_amp;
+            jt.inten[w] = jb.intensity;
+            jt.loss[w] = jb.loss_out;
+            scales[w] = jb.scale;
+        }
+        Plan P;
+        char* gws = (char*)ws + g.ws_off;
+        rc = prepare(&q, op, nullptr, nullptr, gws, g.ws_bytes, gs, &P, nullptr, nullptr, nullptr, &jt);
+        if (rc) return rc;
+        if (op == MSLICE_OP_LOSS_GRAD) {
+            P.base.scale = scales[0];
+            for (int w = 0; w < g.n; ++w) P.base.scales[w] = scales[w];
+            P.base.loss_out = totals + k;
+            rc = run_gradient(&q, P, true, gs);
+        } else {
+            rc = run_forward(&q, P, nullptr, nullptr, gs);
+        }
+        if (rc) return rc;
+    }
+    if (lanes > 1) {
+        for (int l = 0; l < lanes; ++l) {
+            if (note(cudaEventRecord(L->join[l], L->s[l]), "cudaEventRecord") ||
+                note(cudaStreamWaitEvent(st, L->join[l], 0), "cudaStreamWaitEvent"))
+                return MSLICE_ELAUNCH;
+        }
+    }
+    if (op == MSLICE_OP_LOSS_GRAD && loss_total) {
+        k_sum_doubles<<<1, 1, 0, st>>>(totals, (int)G.size(), loss_total);
+        if (note(cudaGetLastError(), "k_sum_doubles launch")) return MSLICE_ELAUNCH;
+    }
+    return MSLICE_OK;
+}
+
 // Allocation-free forward: the workspace is a fixed file-scope device array.
 // Host code must not use g_static_ws directly (its host-side name is a stand-in,
 // not a device address); its device address is taken once per device with
@@ -672,31 +943,15 @@ int mslice_forward(const mslice_params* p, const float* vol, const float* probe,
                    float* field_out, void* ws, size_t ws_bytes, void* stream) {
     cudaStream_t st = (cudaStream_t)stream;
     Plan P;
-    int rc = prepare(p, MSLICE_OP_FORWARD, vol, probe, ws, ws_bytes, st, &P);
-    if (rc) return rc;
+    if (!p) return MSLICE_EINVAL;
     if (!intensity && !field_out) return MSLICE_EINVAL;
-    const double u = (double)p->nw * p->ny * p->nz;
-    SweepArgs a = P.base;
-    a.intensity = intensity;
-    a.field_out = (float2*)field_out;
-    a.j_begin = 0;
-    if (p->ns > 1) {
-        a.j_end = p->ns - 1;
-        a.prop_last = 1;
-        if ((rc = launch_coop(P.ks.fwd, P.grid, P.smem, a, st, KID_FWD, u * (p->ns - 1)))) return rc;
-    }
-    a.j_end = p->ns;
-    if (p->flags & MSLICE_EXIT_WAVE) {
-        // the last propagation is a half step (one-pass: only the factors after
-        // the last transmission; slice ns-2's second factor is a full step)
-        if (P.tab_half) {
-            if (P.ks.one_pass) a.tab2 = P.tab_half;
-            else a.tab = P.tab_half;
-        }
-        return launch_coop(P.ks.last_exit, P.grid, P.smem, a, st, KID_LAST, u);
-    }
-    return launch_coop(P.ks.last_far, P.grid, P.smem, a, st, KID_LAST, u);
+    const JobTable jt = contiguous_table(p, vol, nullptr, nullptr, intensity);
+    int rc = prepare(p, MSLICE_OP_FORWARD, vol, probe, ws, ws_bytes, st, &P, nullptr, nullptr, nullptr,
+                     (p->flags & MSLICE_PER_STRUCTURE) ? &jt : nullptr);
+    if (rc) return rc;
+    return run_forward(p, P, intensity, field_out, st);
 }
+
 
 int mslice_forward_static(const mslice_params* p, const float* vol, const float* probe, float* intensity,
                           float* field_out, void* stream) {
@@ -720,8 +975,11 @@ int mslice_adjoint(const mslice_params* p, const float* vol, const float* probe,
     cudaStream_t st = (cudaStream_t)stream;
     if (!g_psi || !grad_vol) return MSLICE_EINVAL;
     if (p && (p->flags & MSLICE_EXIT_WAVE)) return MSLICE_EUNSUPPORTED;
+    if (!p) return MSLICE_EINVAL;
     Plan P;
-    int rc = prepare(p, MSLICE_OP_ADJOINT, vol, probe, ws, ws_bytes, st, &P);
+    const JobTable jt = contiguous_table(p, vol, grad_vol, nullptr, nullptr);
+    int rc = prepare(p, MSLICE_OP_ADJOINT, vol, probe, ws, ws_bytes, st, &P, nullptr, nullptr, nullptr,
+                     (p->flags & MSLICE_PER_STRUCTURE) ? &jt : nullptr);
     if (rc) return rc;
     P.base.gpsi = (const float2*)g_psi;
     P.base.grad = (float2*)grad_vol;
@@ -734,8 +992,11 @@ int mslice_loss_grad(const mslice_params* p, const float* vol, const float* prob
     cudaStream_t st = (cudaStream_t)stream;
     if (!meas_amp || !loss_out || !grad_vol || !(scale > 0.f)) return MSLICE_EINVAL;
     if (p && (p->flags & MSLICE_EXIT_WAVE)) return MSLICE_EUNSUPPORTED;
+    if (!p) return MSLICE_EINVAL;
     Plan P;
-    int rc = prepare(p, MSLICE_OP_LOSS_GRAD, vol, probe, ws, ws_bytes, st, &P);
+    const JobTable jt = contiguous_table(p, vol, grad_vol, meas_amp, intensity);
+    int rc = prepare(p, MSLICE_OP_LOSS_GRAD, vol, probe, ws, ws_bytes, st, &P, nullptr, nullptr, nullptr,
+                     (p->flags & MSLICE_PER_STRUCTURE) ? &jt : nullptr);
     if (rc) return rc;
     P.base.meas = meas_amp;
     P.base.scale = scale;
@@ -757,7 +1018,8 @@ int mslice_loss_grad_multi(const mslice_params* p, const float* vols, const floa
     for (int w = 0; w < q.nw; ++w)
         if (!(scales[w] > 0.f)) return MSLICE_EINVAL;
     Plan P;
-    int rc = prepare(&q, MSLICE_OP_LOSS_GRAD, vols, probe, ws, ws_bytes, st, &P);
+    const JobTable jt = contiguous_table(&q, vols, grad_vol, meas_amp, intensity);
+    int rc = prepare(&q, MSLICE_OP_LOSS_GRAD, vols, probe, ws, ws_bytes, st, &P, nullptr, nullptr, nullptr, &jt);
     if (rc) return rc;
     P.base.meas = meas_amp;
     P.base.scale = scales[0];
@@ -766,6 +1028,64 @@ int mslice_loss_grad_multi(const mslice_params* p, const float* vols, const floa
     P.base.grad = (float2*)grad_vol;
     P.base.intensity = intensity;
     return run_gradient(&q, P, true, st);
+}
+
+size_t mslice_batched_workspace_size(const mslice_params* common, const mslice_job* jobs, int njobs, int op,
+                                     int lanes) {
+    if (op != MSLICE_OP_FORWARD && op != MSLICE_OP_LOSS_GRAD) return 0;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        sms = 152;
+    std::vector<Group> G;
+    size_t total = 0;
+    if (plan_batch(common, jobs, njobs, op, lanes, G, &total, sms)) return 0;
+    return total;
+}
+
+int mslice_batched_plan(const mslice_params* common, const mslice_job* jobs, int njobs, int op, int lanes,
+                        int* group_of_job, int* lane_of_group, int* ngroups) {
+    if (!ngroups) return MSLICE_EINVAL;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        sms = 152;
+    std::vector<Group> G;
+    size_t total = 0;
+    const int rc = plan_batch(common, jobs, njobs, op, lanes, G, &total, sms);
+    if (rc) return rc;
+    *ngroups = (int)G.size();
+    for (size_t k = 0; k < G.size(); ++k) {
+        if (lane_of_group) lane_of_group[k] = G[k].lane;
+        if (group_of_job)
+            for (int w = 0; w < G[k].n; ++w) group_of_job[G[k].idx[w]] = (int)k;
+    }
+    return MSLICE_OK;
+}
+
+int mslice_batched_status(const mslice_params* common, const mslice_job* jobs, int njobs, int op, int lanes,
+                          const void* ws, void* stream) {
+    if (!ws) return MSLICE_EINVAL;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return MSLICE_ELAUNCH;
+    std::vector<Group> G;
+    size_t total = 0;
+    int rc = plan_batch(common, jobs, njobs, op, lanes, G, &total, sms);
+    if (rc) return rc;
+    for (const Group& g : G) {
+        rc = mslice_status((const char*)ws + g.ws_off, stream);
+        if (rc) return rc;
+    }
+    return MSLICE_OK;
+}
+
+int mslice_loss_grad_batched(const mslice_params* common, const mslice_job* jobs, int njobs, int lanes,
+                             double* loss_total, void* ws, size_t ws_bytes, void* stream) {
+    return run_batch(common, jobs, njobs, lanes, MSLICE_OP_LOSS_GRAD, loss_total, ws, ws_bytes, (cudaStream_t)stream);
+}
+
+int mslice_forward_batched(const mslice_params* common, const mslice_job* jobs, int njobs, int lanes, void* ws,
+                           size_t ws_bytes, void* stream) {
+    return run_batch(common, jobs, njobs, lanes, MSLICE_OP_FORWARD, nullptr, ws, ws_bytes, (cudaStream_t)stream);
 }
 
 int mslice_plan_tables(const mslice_params* p, float* py, float* pz, float* probe_z, void* ws, size_t ws_bytes,

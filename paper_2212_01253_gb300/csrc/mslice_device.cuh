@@ -475,7 +475,16 @@ struct SweepArgs {
     const float2* p2d;      // [nz][ny] angular-spectrum propagator / (ny nz) (AS kernels only)
     const float2* tab2;     // one-pass kernels: table whose P parts serve the last slice's
                             // post-transmission propagation (half steps), or null
+    double* loss_task;      // one-pass loss: FP64 partial of every task of the detector pass
+    double* loss_wsum;      // one-pass loss: per-wavefield sums [nw]
     float scales[MSLICE_MAX_ANGLES];  // per-wavefield loss scale when per_w
+    // one-pass kernels, per-structure runs (per_w): every structure's own
+    // buffers, so that structures need not be contiguous
+    const float2* volw[MSLICE_MAX_ANGLES];   // [ns][nz][ny] delta + i beta (exact adjoint factor)
+    float2* gradw[MSLICE_MAX_ANGLES];        // [ns][nz][ny] gradient out
+    const float* measw[MSLICE_MAX_ANGLES];   // [nz][ny] detector amplitudes
+    float* intw[MSLICE_MAX_ANGLES];          // [nz][ny] intensity out (entries may be null)
+    double* lossw[MSLICE_MAX_ANGLES];        // per-structure loss out (entries may be null)
 };
 
 // transmission row / gradient row of wavefield w at slice j, row z

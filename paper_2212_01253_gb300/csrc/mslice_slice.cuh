@@ -54,6 +54,8 @@ enum : int {
 };
 
 __host__ __device__ __forceinline__ int pass_axis(int j) { return j & 1; }
+// threads of a column group of 2^lcw columns of T threads
+__host__ __device__ __forceinline__ int gthreads_of(int lcw, int T) { return (1 << lcw) * T; }
 
 // shared-memory tables of the one-pass kernels: Wt_y | Wt_z | P_y/ny | P_z/nz
 // [| P2_y/ny | P2_z/nz from tab2]
@@ -131,7 +133,6 @@ __device__ void pass(const SweepArgs& A, const Smem2& S, double* s_red, const in
     }
     // element m of the task sits at plane offset e0 + m * es
     const size_t es = AX == 0 ? (size_t)T : (size_t)T * ny;
-    double loss = 0.0;
     // rows: the teams of a warp iterate together, so that __syncwarp sees every
     // lane: team tm runs while the warp's first task (task - tm) is in range
     const int tlim = AX == 0 ? ntasks + task0 % tpt : ntasks;
@@ -252,8 +253,8 @@ __device__ void pass(const SweepArgs& A, const Smem2& S, double* s_red, const in
                             // factor (1 - conj(v)) (exact); the loads of a chunk of a_j are
                             // issued before the chunk's stores
                             const float2* a = A.seg + (size_t)(j - A.seg_base) * nw * npx + fo;
-                            float2* gdst = (nw == 1 || A.per_w) ? (A.grad + vo)
-                                                                : (A.gpart + (size_t)(j & 1) * nw * npx + fo);
+                            float2* gdst = A.per_w ? (A.gradw[w] + (size_t)j * npx + e0)
+                                           : (nw == 1 ? (A.grad + vo) : (A.gpart + (size_t)(j & 1) * nw * npx + fo));
                             if (!A.exact) {
 #pragma unroll
                                 for (int c0 = 0; c0 < 32; c0 += MS_ADJ_CHUNK) {
@@ -272,7 +273,7 @@ __device__ void pass(const SweepArgs& A, const Smem2& S, double* s_red, const in
                                     }
                                 }
                             } else {
-                                const float2* vv = A.vol + vo;
+                                const float2* vv = A.per_w ? (A.volw[w] + (size_t)j * npx + e0) : (A.vol + vo);
 #pragma unroll
                                 for (int c0 = 0; c0 < 32; c0 += 8) {
                                     float2 av[8], vk[8];
@@ -326,6 +327,8 @@ __device__ void pass(const SweepArgs& A, const Smem2& S, double* s_red, const in
 #pragma unroll
                 for (int m = 0; m < 32; ++m) if (m < P) x[m] = __ldcg(A.field + fo + m * es);
             }
+            // intensity out: the structure's own buffer (per_w) or [nw][nz][ny]
+            float* iout = A.per_w ? (A.intw[w] ? A.intw[w] + e0 : nullptr) : (A.intensity ? A.intensity + fo : nullptr);
             if constexpr (OP == P_EXIT) {
                 propagate<false>(x, N, T, t, reg, W, S.P2[AX], sync);
                 if (active) {
@@ -333,30 +336,31 @@ __device__ void pass(const SweepArgs& A, const Smem2& S, double* s_red, const in
                     for (int m = 0; m < 32; ++m) {
                         if (m < P) {
                             if (A.field_out) __stcs(A.field_out + fo + m * es, x[m]);
-                            if (A.intensity) __stcs(A.intensity + fo + m * es, fmaf(x[m].x, x[m].x, x[m].y * x[m].y));
+                            if (iout) __stcs(iout + m * es, fmaf(x[m].x, x[m].x, x[m].y * x[m].y));
                         }
                     }
                 }
                 continue;
             } else {
                 fft<false>(x, N, T, t, reg, W, sync);
+                const float* mamp = A.per_w ? A.measw[w] + e0 : A.meas + fo;
+                double tl = 0.0;   // this thread's share of the task's loss
 #pragma unroll
                 for (int m = 0; m < 32; ++m) {
                     if (m < P) {
                         const float2 psi = cscale(x[m], ff);
                         const float I = fmaf(psi.x, psi.x, psi.y * psi.y);
-                        const size_t o = fo + m * es;
                         if (active) {
-                            if (A.intensity) __stcs(A.intensity + o, I);
-                            if (A.field_out) __stcs(A.field_out + o, psi);
+                            if (iout) __stcs(iout + m * es, I);
+                            if (A.field_out) __stcs(A.field_out + fo + m * es, psi);
                         }
                         if constexpr (OP == P_FAR_LOSS) {
                             float2 gs = make_float2(0.f, 0.f);
                             if (active) {
                                 const float sc = A.per_w ? A.scales[w] : A.scale;
                                 const float r = sqrtf(sc * I);
-                                const float d = r - __ldg(A.meas + o);
-                                loss += (double)d * (double)d;
+                                const float d = r - __ldg(mamp + m * es);
+                                tl += (double)d * (double)d;
                                 if (r > 0.f) gs = cscale(psi, 2.f * sc * d / r);
                             }
                             x[m] = gs;
@@ -364,6 +368,24 @@ __device__ void pass(const SweepArgs& A, const Smem2& S, double* s_red, const in
                     }
                 }
                 if constexpr (OP == P_FAR_LOSS) {
+                    // the task's loss: summed over the team in a fixed order
+                    // (xor butterfly in the warp, then the group's warps in
+                    // order), one FP64 partial per task
+                    const int span = AX == 0 ? T : gthreads_of(lcw, T);
+                    for (int o = (span < 32 ? span : 32) >> 1; o > 0; o >>= 1) tl += __shfl_xor_sync(0xffffffffu, tl, o);
+                    if (span > 32) {
+                        const int g = threadIdx.x / span, gw = span >> 5;
+                        sync();
+                        if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = tl;
+                        sync();
+                        if ((threadIdx.x & (span - 1)) == 0) {
+                            double sum = 0.0;
+                            for (int i = 0; i < gw; ++i) sum += s_red[g * gw + i];
+                            A.loss_task[task] = sum;
+                        }
+                    } else if (t == 0 && c == 0 && task < ntasks) {
+                        A.loss_task[task] = tl;
+                    }
                     fft<true>(x, N, T, t, reg, W, sync);
                     if (active) {
 #pragma unroll
@@ -372,19 +394,6 @@ __device__ void pass(const SweepArgs& A, const Smem2& S, double* s_red, const in
                     }
                 }
             }
-        }
-    }
-    if constexpr (OP == P_FAR_LOSS) {
-        // block reduction of the FP64 loss partial, fixed order
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) loss += __shfl_xor_sync(0xffffffffu, loss, o);
-        __syncthreads();
-        if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = loss;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double s = 0.0;
-            for (int i = 0; i < MS_WARPS; ++i) s += s_red[i];
-            A.partials[blockIdx.x] = s;
         }
     }
 }
@@ -518,10 +527,24 @@ __global__ void __launch_bounds__(MS_THREADS, 1) k_slice_last(const SweepArgs A)
     if (!grid.sync()) return;
     pass_j<OP2, 0, 0>(A, S, s_red, j, false, true, 1);
     if constexpr (OP2 == P_FAR_LOSS) {
+        // per-wavefield loss: its tasks' partials in task order; then the
+        // total over the wavefields in order (independent of the launch shape
+        // apart from the column-group width, which sets the tasks)
+        if (!grid.sync()) return;
+        const int ax = pass_axis(j) ^ 1;
+        const int ntasks = ax == 0 ? A.nz * A.nw : ((A.ny + (1 << A.lcw) - 1) >> A.lcw) * A.nw;
+        if (threadIdx.x == 0) {
+            for (int w = blockIdx.x; w < A.nw; w += gridDim.x) {
+                double sum = 0.0;
+                for (int tk = w; tk < ntasks; tk += A.nw) sum += __ldcg(A.loss_task + tk);
+                A.loss_wsum[w] = sum;
+                if (A.per_w && A.lossw[w]) *A.lossw[w] = sum;
+            }
+        }
         if (!grid.sync()) return;
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             double sum = 0.0;
-            for (unsigned b = 0; b < gridDim.x; ++b) sum += __ldcg(A.partials + b);
+            for (int w = 0; w < A.nw; ++w) sum += __ldcg(A.loss_wsum + w);
             *A.loss_out = sum;
         }
     }

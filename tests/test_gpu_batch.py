@@ -37,7 +37,7 @@ def test_batched_equals_single_and_oracle():
     from paper_2212_01253_gb300.batch import BatchedLossGrad
     jobs = _jobs(1)
     bat = BatchedLossGrad(jobs, tune=False)
-    assert len(bat.groups) == 3          # three structures share 64x64x12
+    assert bat.ngroups == 3              # three structures share 64x64x12
     bat.run()
     torch.cuda.synchronize()
     bat.check()
@@ -46,6 +46,7 @@ def test_batched_equals_single_and_oracle():
         L1, g1 = G.loss_grad(jb["geo"], jb["vol_h"], jb["meas_h"][None], jb["scale"])
         total += L1
         assert np.array_equal(bat.grad(i).cpu().numpy(), g1)     # same arithmetic per element
+        assert bat.job_loss(i) == L1
         Lr, gr = oracle.loss_grad(jb["geo"], jb["vol_h"], jb["meas_h"][None], jb["scale"])
         assert G.rel(g1, gr) <= 1e-3
     assert abs(bat.loss() - total) <= 1e-9 * total
@@ -62,8 +63,8 @@ def test_graph_replay_equals_eager(lanes):
     torch.cuda.synchronize()
     eager = [bat.grad(i).clone() for i in range(len(jobs))]
     L_eager = bat.loss()
-    for g in bat.groups:
-        g["grad"].zero_()
+    for jb in bat.jobs:
+        jb["grad"].zero_()
     bat.capture()
     bat.replay()
     torch.cuda.synchronize()
@@ -93,3 +94,82 @@ def test_launch_shape_does_not_change_results():
             assert np.array_equal(out, ref), (g, cw)
     g, cw, sc = autotune.tune(256, 512, 2, force=True)
     assert cw in autotune.col_widths(512) and sc in (1, 2)
+
+
+def _mix(seed, shapes):
+    """A mix of uneven structures in the manner of the 64-structure batch: Si
+    substrate with Au pillars, grids 128..512, 128..1024 slices, 0.1-0.5 deg."""
+    rng = np.random.default_rng(seed)
+    jobs = []
+    for k, (ny, nz, ns) in enumerate(shapes):
+        vol = ci.pillars_large(1000 * seed + k, ny, nz, ns, count=max(4, ny // 16))
+        a = float(rng.uniform(0.1, 0.5))
+        jobs.append(dict(shape=(ny, nz, ns), alpha_deg=a, vol_h=vol, scale=float(rng.uniform(0.5, 2.0)),
+                         geo=oracle.Geometry(ny, nz, ns, alpha_i_deg=(a,))))
+    return jobs
+
+
+MIX = [(512, 512, 1024), (128, 128, 128), (256, 128, 256), (128, 256, 128), (256, 128, 256),
+       (128, 128, 512), (256, 256, 128), (128, 128, 128), (512, 128, 128)]
+
+
+@pytest.fixture(scope="module")
+def mix_with_oracle():
+    """Each job's target: Poisson counts (1e6 in all) of another pillar layout
+    of its shape, as in a reconstruction; its flux scale from the counts."""
+    jobs = _mix(4, MIX)
+    for k, jb in enumerate(jobs):
+        ny, nz, ns = jb["shape"]
+        truth = ci.pillars_large(7000 + k, ny, nz, ns, count=max(4, ny // 16))
+        I_gt = oracle.forward(jb["geo"], truth)[0]
+        jb["meas_h"], jb["scale"] = ci.poisson_target(I_gt, 1e6, seed=k)
+        jb["meas_h"] = jb["meas_h"].astype(np.float32)
+        jb["I_ref"] = oracle.forward(jb["geo"], jb["vol_h"])[0]
+        jb["ref"] = oracle.loss_grad(jb["geo"], jb["vol_h"], jb["meas_h"][None], jb["scale"])
+    return jobs
+
+
+@pytest.mark.parametrize("lanes", [1, 4])
+def test_batched_uneven_mix_vs_oracle_and_single_calls(mix_with_oracle, lanes):
+    """mslice_loss_grad_batched on nine structures of seven shapes (one
+    512x512x1024, one 128x128x128 ...): every job's loss and gradient match
+    the FP64 oracle, and equal the single-structure call bit for bit."""
+    from paper_2212_01253_gb300.batch import BatchedLossGrad
+    jobs = mix_with_oracle
+    dj = [dict(vol=G.dev(jb["vol_h"], np.complex64), meas=G.dev(jb["meas_h"], np.float32), scale=jb["scale"],
+               alpha_deg=jb["alpha_deg"]) for jb in jobs]
+    bat = BatchedLossGrad(dj, tune=False, lanes=lanes)
+    assert bat.ngroups == 7
+    bat.run()
+    torch.cuda.synchronize()
+    bat.check()
+    total = 0.0
+    for i, jb in enumerate(jobs):
+        L_ref, g_ref = jb["ref"]
+        g = bat.grad(i).cpu().numpy()
+        L = bat.job_loss(i)
+        total += L
+        assert abs(L - L_ref) <= 1e-4 * abs(L_ref), (jb["shape"], L, L_ref)
+        assert G.rel(g, g_ref) <= 1e-3, jb["shape"]
+        L1, g1 = G.loss_grad(jb["geo"], jb["vol_h"], jb["meas_h"][None], jb["scale"])
+        assert L == L1 and np.array_equal(g, g1), jb["shape"]
+    assert bat.loss() == pytest.approx(total, rel=1e-12)
+
+
+def test_forward_batched_vs_oracle_and_single_calls(mix_with_oracle):
+    from paper_2212_01253_gb300 import binding as B
+    jobs = mix_with_oracle
+    dj = [dict(vol=G.dev(jb["vol_h"], np.complex64), alpha_deg=jb["alpha_deg"],
+               intensity=torch.full(jb["shape"][1::-1], float("nan"), dtype=torch.float32, device="cuda"))
+          for jb in jobs]
+    common = B.make_params(64, 64, 1)
+    arr = B.make_jobs(dj)
+    ws = torch.empty(B.mslice_batched_workspace_size(common, arr, B.MSLICE_OP_FORWARD, 3), dtype=torch.uint8,
+                     device="cuda")
+    B.mslice_forward_batched(common, arr, 3, ws)
+    torch.cuda.synchronize()
+    assert B.mslice_batched_status(common, arr, B.MSLICE_OP_FORWARD, 3, ws) == 0
+    for jb, d in zip(jobs, dj):
+        I = d["intensity"].cpu().numpy()
+        assert G.rel(I, jb["I_ref"]) <= 1e-4, jb["shape"]
+        assert np.array_equal(I, G.forward(jb["geo"], jb["vol_h"])[0])

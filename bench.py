@@ -311,6 +311,39 @@ def run_gpu(args):
     units_step = NY * NZ * ns * nw
     value, ms_max = whole_job_rate(units_step, ms, dev)
 
+    # the same step with a checkpoint every 32 slices and segment recompute
+    # (the schedule that keeps deep stacks small: ns/32 + 32 fields instead of
+    # every a_j), timed the same way
+    ck32 = None
+    if not args.no_ckpt32 and ckpt != 32 and world == 1:
+        p32 = B.make_params(NY, NZ, ns, angles(nw), LAM, SLICE, DY, DZ, 32,
+                            flags=B.MSLICE_ANGULAR if args.angular else 0)
+        p32.grid_blocks, p32.col_width, p32.schedule = p.grid_blocks, p.col_width, p.schedule
+        ws32 = torch.empty(B.mslice_workspace_size(p32, B.MSLICE_OP_LOSS_GRAD), dtype=torch.uint8, device=dev)
+        loss32 = torch.zeros(1, dtype=torch.float64, device=dev)
+
+        def step32():
+            B.mslice_loss_grad(p32, vol, None, meas, s, loss32, grad, None, ws32)
+
+        for _ in range(3):
+            step32()
+        n32 = max(3, min(args.steps, 5))
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(n32):
+            step32()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if B.mslice_status(ws32) != 0:
+            raise RuntimeError("device-side wait timed out in the checkpoint-32 leg")
+        ms32 = e0.elapsed_time(e1) / n32
+        ck32 = {"checkpoint_every": 32, "ms_per_step": ms32, "value": units_step / (ms32 / 1e3), "unit": UNIT,
+                "steps": n32, "warmup": 3, "ratio_to_headline": ms32 / ms,
+                "workspace_gb": ws32.numel() / 1e9, "headline_workspace_gb": ws.numel() / 1e9,
+                "loss_matches_headline": bool(abs(float(loss32.item()) - float(loss.item()))
+                                              <= 1e-12 * abs(float(loss.item())))}
+        del ws32
+
     # end to end through the public API with host buffers
     e2e = None
     if not args.no_e2e:
@@ -403,7 +436,9 @@ def run_gpu(args):
                                                          "schedule": p.schedule},
                            propagator="angular spectrum" if args.angular else "paraxial (Eq. 1)"),
             "roofline": roofline, "effective_hbm": hbm, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
-            "gpu_launches": gpu_launches, "kernels": kernels, "loss": float(loss.item())}
+            "gpu_launches": gpu_launches, "kernels": kernels, "loss": float(loss.item()),
+            "checkpoint32": ck32,
+            "recon": None if (args.no_recon or world > 1) else recon_leg(args, dev)}
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -498,6 +533,65 @@ def run_batch(args):
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def recon_leg(args, dev):
+    """Reconstruction at 256x256x512 with a checkpoint every 32 slices: wall
+    time to chi2_red <= 1.1 chi2_red(truth) of one held-out pillar layout from
+    the learned start (network trained here on fresh forward-model samples,
+    inference included) and from the zero start (bare substrate), each capped
+    at args.recon_cap iterations."""
+    import torch
+
+    import cssi_inputs as ci
+    from paper_2212_01253_gb300 import binding as B
+    from paper_2212_01253_gb300.learned import ARCH_256, EncoderDecoder, PillarSampler, train
+    from paper_2212_01253_gb300.recon import Reconstructor
+
+    ny = nz = 256
+    ns = 512
+    shape, block, off = (64, 64, 64), (8, 2, 4), (0, 128, 0)
+    p = B.make_params(ny, nz, ns, (0.3,), checkpoint_every=32)
+    c = B.make_coarse(shape, block, off)
+    base = torch.from_numpy(ci.substrate(ny, nz, ns)).to(dev)
+    batch = 64
+    sampler = PillarSampler(p, c, base, n_pillars=(4, 16), foot=(2, 9), height=(1, 9), chunk=args.chunk,
+                            tune=not args.no_tune)
+    net = EncoderDecoder(ARCH_256, batch)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    train(net, sampler, args.recon_train_samples, batch, lr=1e-3, seed=1000)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    seed = 200000
+    meas, sc, chi2_gt, _ = _pillar_case(B, ci, torch, p, c, base, sampler, seed)
+    measd = torch.from_numpy(meas).to(dev)
+    out = {}
+    for name in ("learned", "zero"):
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        th0 = None if name == "zero" else net.predict(sampler.features_of(measd)).reshape(-1).contiguous()
+        torch.cuda.synchronize()
+        t_init = time.perf_counter() - t1
+        R = Reconstructor(p, c, base, measd, sc, theta0=th0, lr=args.lr)
+        it, sec, hist = R.run(chi2_target=1.1 * chi2_gt, max_iters=args.recon_cap, check_every=5)
+        out[name] = {"seconds": t_init + sec, "iterations": it,
+                     "reached": bool(hist and hist[-1][1] <= 1.1 * chi2_gt),
+                     "chi2_start": hist[0][1] if hist else None, "chi2_end": hist[-1][1] if hist else None,
+                     "ms_per_iteration": 1e3 * sec / it, "init_seconds": t_init}
+    ratio = out["zero"]["seconds"] / out["learned"]["seconds"]
+    return {"metric": "recon wall time to chi2_red <= 1.1 chi2_red(truth)", "unit": "s",
+            "chi2_truth": chi2_gt, "target": 1.1 * chi2_gt, "cap_iterations": args.recon_cap,
+            "learned": out["learned"], "zero": out["zero"],
+            "zero_over_learned": ratio,
+            "ratio_kind": ("measured (both reached the target)" if out["zero"]["reached"] and out["learned"]["reached"]
+                           else "lower bound (the zero start did not reach the target within the cap)"
+                           if out["learned"]["reached"] else "learned start did not reach the target"),
+            "training": {"samples": args.recon_train_samples, "seconds": t_train, "batch": batch},
+            "config": {"workload": "256x256 grid (2 nm), 512 slices of 20 nm, 0.3 deg, checkpoint every 32 "
+                                   "slices; 64^3 coarse delta (8x2x4 fine voxels, top half); held-out layout of "
+                                   "4-16 Au pillars (seed %d), Poisson target 1e6 counts; ADAM lr %g"
+                                   % (seed, args.lr)}}
 
 
 def run_recon(args):
@@ -904,6 +998,11 @@ def main():
     ap.add_argument("--jobs", type=int, default=64)
     ap.add_argument("--lanes", type=int, default=4, help="batch: concurrent streams, SMs split between them")
     ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--no-ckpt32", action="store_true", help="sweep: skip the checkpoint-every-32 leg")
+    ap.add_argument("--no-recon", action="store_true", help="sweep: skip the reconstruction leg")
+    ap.add_argument("--recon-train-samples", type=int, default=65536,
+                    help="sweep: forward-model samples the reconstruction leg's network trains on")
+    ap.add_argument("--recon-cap", type=int, default=3000, help="sweep: iteration cap of the reconstruction leg")
     ap.add_argument("--angular", action="store_true", help="sweep: angular-spectrum propagator instead of Eq. 1's")
     ap.add_argument("--lr", type=float, default=2e-6)
     ap.add_argument("--max-iters", type=int, default=300)

@@ -65,7 +65,7 @@ class OrcParams(ctypes.Structure):
         ("force_naive_dft", ctypes.c_int32),
         ("exit_wave", ctypes.c_int32),
         ("exact", ctypes.c_int32),
-        ("psi_rad", ctypes.c_double),
+        ("psi_rad", ctypes.POINTER(ctypes.c_double)),
         ("strang", ctypes.c_int32),
         ("angular", ctypes.c_int32),
     ]
@@ -110,7 +110,10 @@ class Geometry:
         self.angular = bool(angular)
         # exact 1 - n^2 in the transmission of Eq. 1 instead of 2 (delta - i beta)
         self.exact_transmission = bool(exact_transmission)
-        self.psi_rad = float(np.deg2rad(psi_deg))      # in-plane angle of the default probe
+        # in-plane angle of each view's default probe (one value for all views,
+        # or one per incidence angle)
+        self.psi_rad_w = np.deg2rad(np.broadcast_to(np.asarray(psi_deg, dtype=np.float64),
+                                                    np.atleast_1d(np.asarray(alpha_i_deg)).shape)).copy()
         self.wavelength_nm = float(wavelength_nm)
         self.slice_nm = float(slice_nm)
         self.dy_nm, self.dz_nm = float(dy_nm), float(dz_nm)
@@ -120,12 +123,19 @@ class Geometry:
     def nw(self):
         return int(self.alpha_i_rad.size)
 
+    @property
+    def psi_rad(self):
+        """The in-plane angle when all views share one, else the per-view array."""
+        return float(self.psi_rad_w[0]) if np.all(self.psi_rad_w == self.psi_rad_w[0]) else self.psi_rad_w
+
     def _params(self, naive=False, exit_wave=False):
         self._alpha_keep = np.ascontiguousarray(self.alpha_i_rad, dtype=np.float64)
+        self._psi_keep = np.ascontiguousarray(self.psi_rad_w, dtype=np.float64)
         return OrcParams(self.wavelength_nm, self.slice_nm, self.dy_nm, self.dz_nm,
                          self.ny, self.nz, self.ns, self.nw,
                          self._alpha_keep.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
-                         int(bool(naive)), int(bool(exit_wave)), int(self.exact_transmission), self.psi_rad,
+                         int(bool(naive)), int(bool(exit_wave)), int(self.exact_transmission),
+                         self._psi_keep.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                          int(self.strang), int(self.angular))
 
 

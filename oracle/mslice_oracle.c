@@ -90,7 +90,8 @@ typedef struct {
     int32_t force_naive_dft;  /* 1: use the O(N^2) DFT at every size */
     int32_t exit_wave;        /* 1: forward returns phi_Ns (full last propagation) instead of Psi */
     int32_t exact;            /* 1: exact 1 - n^2 in the transmission instead of 2 (delta - i beta) */
-    double psi_rad;           /* in-plane angle: the default probe also carries exp(-i k sin(psi) y) */
+    const double *psi_rad;    /* [nw] in-plane angle of each wavefield (NULL: 0): the default probe
+                                 of wavefield w also carries exp(-i k sin(psi_w) y) */
     int32_t strang;           /* 1: symmetric splitting (half steps of propagation at both ends) */
     int32_t angular;          /* 1: angular-spectrum propagator instead of the paraxial one */
 } orc_params;
@@ -256,10 +257,11 @@ static void initial_field(const orc_params *q, const cplx *probe, int w, cplx *p
     }
     const double k = 2.0 * M_PI / q->wavelength_nm;
     double alpha = q->alpha_i_rad ? q->alpha_i_rad[w] : 0.0;
+    double psi = q->psi_rad ? q->psi_rad[w] : 0.0;
     for (int l = 0; l < q->nz; l++)
         for (int m = 0; m < q->ny; m++)
             phi[(size_t)l * q->ny + m] =
-                cexp(-I * k * (sin(alpha) * ((double)l * q->dz_nm) + sin(q->psi_rad) * ((double)m * q->dy_nm)));
+                cexp(-I * k * (sin(alpha) * ((double)l * q->dz_nm) + sin(psi) * ((double)m * q->dy_nm)));
 }
 
 /* phi <- F^-1 [ P F phi ]  (conj_p: use conj(P), the adjoint) */

@@ -534,3 +534,22 @@ def test_propagator_tables_move_a_basis_mode_by_their_product(oracle_lib):
         assert abs(py[a] * pz[b] - closed) < 1e-13, (a, b)
         assert abs(py[a] - np.exp(-1j * delta * LAM * np.pi * fy * fy)) < 1e-13
         assert abs(pz[b] - np.exp(-1j * delta * LAM * np.pi * fz * fz)) < 1e-13
+
+
+def test_per_view_in_plane_angles_land_in_their_own_bins(oracle_lib):
+    """Eq. 2-3 with one in-plane angle per view: view w's default probe with
+    sin(psi_w) = m_w lambda / (ny dy) is the DFT basis vector of bin -m_w, so
+    through vacuum all of view w's intensity lands in column (ny - m_w) mod ny
+    of row 0, whatever the other views' angles."""
+    ny, nz = 64, 16
+    ms = (5, -3, 0)
+    psi = [np.rad2deg(np.arcsin(m * 0.155 / (ny * 2.0))) for m in ms]
+    geo = oracle_lib.Geometry(ny, nz, 2, alpha_i_deg=(0.0, 0.0, 0.0), psi_deg=psi)
+    I = oracle_lib.forward(geo, np.zeros((2, nz, ny)))
+    for w, m in enumerate(ms):
+        assert I[w, 0, (ny - m) % ny] == pytest.approx(ny * nz, rel=1e-12)
+        assert I[w].sum() == pytest.approx(ny * nz, rel=1e-12)
+    # the same views one at a time agree bit for bit
+    for w in range(3):
+        g1 = oracle_lib.Geometry(ny, nz, 2, alpha_i_deg=(0.0,), psi_deg=psi[w])
+        assert np.array_equal(oracle_lib.forward(g1, np.zeros((2, nz, ny)))[0], I[w])

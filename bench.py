@@ -614,7 +614,9 @@ def run_recon(args):
     # sharing the volume (loss and gradient summed over the views)
     ang = (0.3,) if args.recon_angles <= 1 else tuple(np.linspace(0.1, 0.5, args.recon_angles))
     nw = len(ang)
-    p = B.make_params(ny, nz, ns, ang, checkpoint_every=ns)   # every a_j kept
+    # in-plane angle of each view: 0, or swept over [-recon_psi, recon_psi] deg
+    psi = np.deg2rad(np.linspace(-args.recon_psi, args.recon_psi, nw)) if nw > 1 else np.zeros(1)
+    p = B.make_params(ny, nz, ns, ang, checkpoint_every=ns, psi_rad=psi)   # every a_j kept
     c = B.make_coarse(shape, block, off)
     rng = np.random.default_rng(0)
     truth = np.zeros(shape, np.float32)
@@ -647,8 +649,9 @@ def run_recon(args):
             "dtype": "f32", "data": "synthetic",
             "config": {"workload": "256x256 grid, 512 slices, %s, 64^3 coarse delta (8x2x4 fine voxels each, "
                                    "top half), Poisson targets 1e6 counts per view, zero (bare substrate) start, "
-                                   "ADAM lr %g" % ("%d views %.2f-%.2f deg" % (nw, ang[0], ang[-1]) if nw > 1
-                                                   else "0.3 deg", args.lr)}}
+                                   "ADAM lr %g" % ("%d views %.2f-%.2f deg, in-plane %+.2f..%+.2f deg"
+                                                   % (nw, ang[0], ang[-1], -args.recon_psi, args.recon_psi)
+                                                   if nw > 1 else "0.3 deg", args.lr)}}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -993,6 +996,8 @@ def main():
     ap.add_argument("--shrinkwrap-sigma", type=float, default=1.0, help="buried: shrink-wrap blur (coarse voxels)")
     ap.add_argument("--shrinkwrap-threshold", type=float, default=0.2, help="buried: shrink-wrap threshold")
     ap.add_argument("--recon-angles", type=int, default=1, help="recon: incidence angles (views) sharing the volume")
+    ap.add_argument("--recon-psi", type=float, default=0.0,
+                    help="recon: in-plane angles of the views swept over [-psi, psi] deg")
     ap.add_argument("--checkpoint", type=int, default=0,
                     help="adjoint checkpoint interval (0: keep every a_j when it fits in half the HBM, else 32)")
     ap.add_argument("--jobs", type=int, default=64)

@@ -14,10 +14,10 @@
  *     free propagation to the detector are pure Fourier phases and are skipped).
  *   Eq. 4 (Sec. 4.1): the loss is the squared error of amplitudes; this library
  *     sums it (no 1/N): L = sum (sqrt(s I) - m)^2, m = sqrt(I_meas).
- *   Sec. 2, Eq. 2-3: the incidence angle alpha_i and the in-plane angle psi are
- *     applied by tilting the probe, phi_0(y, z) = exp(-i k (sin(alpha_i) z +
- *     sin(psi) y)) (toward the substrate for alpha_i > 0), instead of rotating
- *     the volume (paraxially equivalent).
+ *   Sec. 2, Eq. 2-3: the incidence angle alpha_i and the in-plane angle psi of
+ *     each wavefield (view) are applied by tilting its probe, phi_0(y, z) =
+ *     exp(-i k (sin(alpha_i) z + sin(psi) y)) (toward the substrate for
+ *     alpha_i > 0), instead of rotating the volume (paraxially equivalent).
  *
  * Axes and layouts (all arrays row-major, last index fastest):
  *   x  = slice index along the beam, ns slices of thickness slice_nm (Delta);
@@ -110,9 +110,9 @@ typedef struct mslice_params {
     int32_t ns;                /* number of slices, >= 1 */
     int32_t nw;                /* number of wavefields (incidence angles), 1..MSLICE_MAX_ANGLES */
     double alpha_i_rad[MSLICE_MAX_ANGLES]; /* incidence angle of each wavefield */
-    double psi_rad;            /* in-plane (yaw) angle of the beam, |psi| < 0.1 rad: the default
-                                  probe carries the phase exp(-i k sin(psi) y) (user probes
-                                  are used as given) */
+    double psi_rad[MSLICE_MAX_ANGLES]; /* in-plane (yaw) angle of each wavefield's beam, |psi| < 0.1
+                                  rad: the default probe of wavefield w carries the phase
+                                  exp(-i k sin(psi_w) y) (user probes are used as given) */
     int32_t checkpoint_every;  /* adjoint segment length in slices; <= 0 means 32 */
     uint32_t flags;            /* MSLICE_EXIT_WAVE, MSLICE_PER_STRUCTURE, MSLICE_EXACT_TRANSMISSION,
                                   MSLICE_STRANG, MSLICE_ANGULAR */
@@ -220,6 +220,7 @@ typedef struct mslice_job {
     int32_t col_width;         /* launch shape of this job's group (the group takes its first job's):
                                   columns per column-pass group, 0 = automatic */
     double alpha_i_rad;        /* incidence angle */
+    double psi_rad;            /* in-plane angle (|psi| < 0.1 rad), as psi_rad of mslice_params */
     float scale;               /* s > 0: model intensity scale of the loss (loss + gradient only) */
     float reserved;            /* 0 */
     const float *vol;          /* [ns][nz][ny] complex delta + i beta, device, 16-byte aligned */
@@ -231,10 +232,11 @@ typedef struct mslice_job {
 
 /* Bytes of workspace of a batched call (op MSLICE_OP_FORWARD or
  * MSLICE_OP_LOSS_GRAD) for these jobs and lanes; 0 if the request is invalid.
- * `common` gives the wavelength, slice thickness, pixel sizes, in-plane angle,
- * checkpoint interval, flags (MSLICE_EXACT_TRANSMISSION, MSLICE_STRANG;
+ * `common` gives the wavelength, slice thickness, pixel sizes, checkpoint
+ * interval, flags (MSLICE_EXACT_TRANSMISSION, MSLICE_STRANG;
  * MSLICE_EXIT_WAVE for the forward) and grid_blocks (used when lanes == 1);
- * its ny, nz, ns, nw and alpha_i_rad are ignored. */
+ * its ny, nz, ns, nw, alpha_i_rad and psi_rad are ignored (every job has its
+ * own grid and angles). */
 size_t mslice_batched_workspace_size(const mslice_params *common, const mslice_job *jobs, int njobs, int op,
                                      int lanes);
 

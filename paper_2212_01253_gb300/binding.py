@@ -48,7 +48,7 @@ class mslice_params(ctypes.Structure):
         ("ns", ctypes.c_int32),
         ("nw", ctypes.c_int32),
         ("alpha_i_rad", ctypes.c_double * MSLICE_MAX_ANGLES),
-        ("psi_rad", ctypes.c_double),
+        ("psi_rad", ctypes.c_double * MSLICE_MAX_ANGLES),
         ("checkpoint_every", ctypes.c_int32),
         ("flags", ctypes.c_uint32),
         ("grid_blocks", ctypes.c_int32),
@@ -60,7 +60,8 @@ class mslice_params(ctypes.Structure):
 def make_params(ny, nz, ns, alpha_i_deg=(0.3,), wavelength_nm=0.155, slice_nm=20.0,
                 dy_nm=2.0, dz_nm=2.0, checkpoint_every=32, flags=0, psi_rad=0.0, grid_blocks=0,
                 col_width=0, schedule=0):
-    """mslice_params from plain numbers (angles in degrees)."""
+    """mslice_params from plain numbers (incidence angles in degrees; psi_rad, the
+    in-plane angle in radians, one value for all wavefields or one per wavefield)."""
     alphas = [math.radians(float(a)) for a in (alpha_i_deg if hasattr(alpha_i_deg, "__len__")
                                                else [alpha_i_deg])]
     if not 1 <= len(alphas) <= MSLICE_MAX_ANGLES:
@@ -70,7 +71,11 @@ def make_params(ny, nz, ns, alpha_i_deg=(0.3,), wavelength_nm=0.155, slice_nm=20
     p.ny, p.nz, p.ns, p.nw = int(ny), int(nz), int(ns), len(alphas)
     for i, a in enumerate(alphas):
         p.alpha_i_rad[i] = a
-    p.psi_rad = psi_rad
+    psis = list(psi_rad) if hasattr(psi_rad, "__len__") else [psi_rad] * len(alphas)
+    if len(psis) != len(alphas):
+        raise ValueError("one in-plane angle, or one per incidence angle")
+    for i, v in enumerate(psis):
+        p.psi_rad[i] = float(v)
     p.checkpoint_every = int(checkpoint_every)
     p.flags = int(flags)
     p.grid_blocks = int(grid_blocks)
@@ -100,7 +105,8 @@ def make_coarse(shape, block, offset=(0, 0, 0), beta_ratio=4.9e-6 / 4.7e-5, base
 
 class mslice_job(ctypes.Structure):
     _fields_ = [("ny", ctypes.c_int32), ("nz", ctypes.c_int32), ("ns", ctypes.c_int32),
-                ("col_width", ctypes.c_int32), ("alpha_i_rad", ctypes.c_double), ("scale", ctypes.c_float),
+                ("col_width", ctypes.c_int32), ("alpha_i_rad", ctypes.c_double), ("psi_rad", ctypes.c_double),
+                ("scale", ctypes.c_float),
                 ("reserved", ctypes.c_float), ("vol", ctypes.c_void_p), ("meas_amp", ctypes.c_void_p),
                 ("grad_vol", ctypes.c_void_p), ("intensity", ctypes.c_void_p), ("loss_out", ctypes.c_void_p)]
 
@@ -117,6 +123,7 @@ def make_jobs(jobs):
         j.ny, j.nz, j.ns = int(ny), int(nz), int(ns)
         j.col_width = int(jb.get("col_width", 0))
         j.alpha_i_rad = math.radians(float(jb["alpha_deg"]))
+        j.psi_rad = float(jb.get("psi_rad", 0.0))
         j.scale = float(jb.get("scale", 1.0))
         j.vol = _ptr(jb["vol"], torch.complex64, ns * nz * ny, "vol")
         j.meas_amp = _ptr(jb.get("meas"), torch.float32, nz * ny, "meas")

@@ -29,11 +29,11 @@ struct SetupArgs {
     int ny, nz, nw;
     double slice_nm, wavelength_nm, dy_nm, dz_nm;
     double sin_alpha[MSLICE_MAX_ANGLES];
-    double sin_psi;
+    double sin_psi[MSLICE_MAX_ANGLES];
     float2* tab;       // Wt_y | Wt_z | P_y/ny | P_z/nz
     float2* tab_half;  // the same with P over Delta/2, or null
     float2* probe_z;   // [nw][nz]
-    float2* probe_y;   // [ny] exp(-i k sin(psi) y_m)
+    float2* probe_y;   // [nw][ny] exp(-i k sin(psi_w) y_m)
     float2* py_out;    // optional, unnormalised
     float2* pz_out;
     float2* probe_z_out;
@@ -60,7 +60,7 @@ __device__ double2 propagator_entry(int m, int n, double d, double slice, double
 
 __global__ void k_setup(const SetupArgs S) {
     const int ny = S.ny, nz = S.nz;
-    const int total = 2 * (ny + nz) + S.nw * nz + ny;
+    const int total = 2 * (ny + nz) + S.nw * (nz + ny);
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
         if (i < ny) {
             S.tab[i] = twiddle_entry(i, ny);
@@ -87,11 +87,12 @@ __global__ void k_setup(const SetupArgs S) {
                 S.tab_half[i] = make_float2((float)(h.x / nz), (float)(h.y / nz));
             }
         } else if (i >= 2 * (ny + nz) + S.nw * nz) {
-            // exp(-i k sin(psi) y_m) = exp(-i pi (2 sin(psi) m dy / lambda))
-            const int m = i - 2 * (ny + nz) - S.nw * nz;
+            // exp(-i k sin(psi_w) y_m) = exp(-i pi (2 sin(psi_w) m dy / lambda))
+            const int q = i - 2 * (ny + nz) - S.nw * nz;
+            const int w = q / ny, m = q % ny;
             double s, c;
-            sincospi(2.0 * S.sin_psi * (double)m * S.dy_nm / S.wavelength_nm, &s, &c);
-            S.probe_y[m] = make_float2((float)c, (float)(-s));
+            sincospi(2.0 * S.sin_psi[w] * (double)m * S.dy_nm / S.wavelength_nm, &s, &c);
+            S.probe_y[q] = make_float2((float)c, (float)(-s));
         } else {
             const int q = i - 2 * (ny + nz);
             const int w = q / nz, l = q % nz;
@@ -209,7 +210,8 @@ int validate(const mslice_params* p) {
     if (!(p->wavelength_nm > 0) || !(p->slice_nm > 0) || !(p->dy_nm > 0) || !(p->dz_nm > 0)) return MSLICE_EINVAL;
     for (int w = 0; w < p->nw; ++w)
         if (!(fabs(p->alpha_i_rad[w]) < 1.5707963)) return MSLICE_EINVAL;
-    if (!(fabs(p->psi_rad) < 0.1)) return MSLICE_EINVAL;
+    for (int w = 0; w < p->nw; ++w)
+        if (!(fabs(p->psi_rad[w]) < 0.1)) return MSLICE_EINVAL;
     if (p->flags & ~(MSLICE_EXIT_WAVE | MSLICE_PER_STRUCTURE | MSLICE_EXACT_TRANSMISSION | MSLICE_STRANG |
                      MSLICE_ANGULAR))
         return MSLICE_EINVAL;
@@ -240,7 +242,7 @@ Layout make_layout(const mslice_params* p, int op) {
     L.partials = off; off = align256(off + kPartialBytes);
     L.tab = off; off = align256(off + 2 * (size_t)(p->ny + p->nz) * sizeof(float2));
     L.probe_z = off; off = align256(off + (size_t)p->nw * p->nz * sizeof(float2));
-    L.probe_y = off; off = align256(off + (size_t)p->ny * sizeof(float2));
+    L.probe_y = off; off = align256(off + (size_t)p->nw * p->ny * sizeof(float2));
     const size_t nvol = (p->flags & MSLICE_PER_STRUCTURE) ? (size_t)p->nw : 1;
     L.tvol = off; off = align256(off + nvol * p->ns * npx * sizeof(float2));
     L.field = off; off = align256(off + fb);
@@ -540,15 +542,17 @@ int prepare(const mslice_params* p, int op, const float* vol, const float* probe
     SetupArgs S{};
     S.ny = p->ny; S.nz = p->nz; S.nw = p->nw;
     S.slice_nm = p->slice_nm; S.wavelength_nm = p->wavelength_nm; S.dy_nm = p->dy_nm; S.dz_nm = p->dz_nm;
-    for (int i = 0; i < p->nw; ++i) S.sin_alpha[i] = sin(p->alpha_i_rad[i]);
-    S.sin_psi = sin(p->psi_rad);
+    for (int i = 0; i < p->nw; ++i) {
+        S.sin_alpha[i] = sin(p->alpha_i_rad[i]);
+        S.sin_psi[i] = sin(p->psi_rad[i]);
+    }
     S.tab = (float2*)(w + L.tab);
     const bool strang = (p->flags & MSLICE_STRANG) != 0;
     S.tab_half = strang ? (float2*)(w + L.tab_half) : nullptr;
     S.probe_z = (float2*)(w + L.probe_z);
     S.probe_y = (float2*)(w + L.probe_y);
     S.py_out = py_out; S.pz_out = pz_out; S.probe_z_out = probe_z_out;
-    const int total = 2 * (p->ny + p->nz) + p->nw * p->nz + p->ny;
+    const int total = 2 * (p->ny + p->nz) + p->nw * (p->nz + p->ny);
     ProfRec* r = prof_begin(KID_SETUP, 0.0, st);
     k_setup<<<(total + 255) / 256, 256, 0, st>>>(S);
     prof_end(r, st);
@@ -579,7 +583,9 @@ int prepare(const mslice_params* p, int op, const float* vol, const float* probe
     a.exact = exact;
     a.probe = (const float2*)probe;
     a.probe_z = (const float2*)(w + L.probe_z);
-    a.probe_y = p->psi_rad != 0.0 ? (const float2*)(w + L.probe_y) : nullptr;
+    bool tilt_y = false;
+    for (int q = 0; q < p->nw; ++q) tilt_y = tilt_y || p->psi_rad[q] != 0.0;
+    a.probe_y = tilt_y ? (const float2*)(w + L.probe_y) : nullptr;
     a.tab = (const float2*)(w + L.tab);
     a.field = (float2*)(w + L.field);
     if (op != MSLICE_OP_FORWARD) {
@@ -747,7 +753,10 @@ mslice_params group_params(const mslice_params* common, const mslice_job* jobs, 
                            int lanes, int sms) {
     mslice_params q = *common;
     q.ny = g.ny; q.nz = g.nz; q.ns = g.ns; q.nw = g.n;
-    for (int k = 0; k < g.n; ++k) q.alpha_i_rad[k] = jobs[g.idx[k]].alpha_i_rad;
+    for (int k = 0; k < g.n; ++k) {
+        q.alpha_i_rad[k] = jobs[g.idx[k]].alpha_i_rad;
+        q.psi_rad[k] = jobs[g.idx[k]].psi_rad;
+    }
     q.flags |= MSLICE_PER_STRUCTURE;
     const int cw = jobs[g.idx[0]].col_width;
     if (cw > 0) q.col_width = cw;
@@ -1100,13 +1109,15 @@ int mslice_plan_tables(const mslice_params* p, float* py, float* pz, float* prob
     SetupArgs S{};
     S.ny = p->ny; S.nz = p->nz; S.nw = p->nw;
     S.slice_nm = p->slice_nm; S.wavelength_nm = p->wavelength_nm; S.dy_nm = p->dy_nm; S.dz_nm = p->dz_nm;
-    for (int i = 0; i < p->nw; ++i) S.sin_alpha[i] = sin(p->alpha_i_rad[i]);
-    S.sin_psi = sin(p->psi_rad);
+    for (int i = 0; i < p->nw; ++i) {
+        S.sin_alpha[i] = sin(p->alpha_i_rad[i]);
+        S.sin_psi[i] = sin(p->psi_rad[i]);
+    }
     S.tab = (float2*)(w + L.tab);
     S.probe_z = (float2*)(w + L.probe_z);
     S.probe_y = (float2*)(w + L.probe_y);
     S.py_out = (float2*)py; S.pz_out = (float2*)pz; S.probe_z_out = (float2*)probe_z;
-    const int total = 2 * (p->ny + p->nz) + p->nw * p->nz + p->ny;
+    const int total = 2 * (p->ny + p->nz) + p->nw * (p->nz + p->ny);
     k_setup<<<(total + 255) / 256, 256, 0, st>>>(S);
     return cudaGetLastError() == cudaSuccess ? MSLICE_OK : MSLICE_ELAUNCH;
 }

@@ -444,7 +444,7 @@ struct SweepArgs {
     const float2* vol;      // [ns][nz][ny] delta + i beta (read by the adjoint when exact)
     const float2* probe;    // [nw][nz][ny] or null
     const float2* probe_z;  // [nw][nz] default probe rows
-    const float2* probe_y;  // [ny] in-plane tilt of the default probe, or null (psi = 0)
+    const float2* probe_y;  // [nw][ny] in-plane tilt of each default probe, or null (every psi = 0)
     const float2* tab;      // Wt_y[ny] | Wt_z[nz] | P_y[ny]/ny | P_z[nz]/nz
     float2* field;          // [nw][nz][ny] forward state
     float2* gfield;         // [nw][nz][ny] adjoint state
@@ -584,7 +584,8 @@ __device__ void row_pass(const SweepArgs& A, const Smem& S, const int j, const b
                     const float2 v = A.probe_z[(size_t)w * A.nz + z];
                     if (A.probe_y) {
 #pragma unroll
-                        for (int m = 0; m < 32; ++m) if (m < P) x[m] = cmul(v, __ldg(A.probe_y + t + T * m));
+                        for (int m = 0; m < 32; ++m)
+                            if (m < P) x[m] = cmul(v, __ldg(A.probe_y + (size_t)w * A.ny + t + T * m));
                     } else {
 #pragma unroll
                         for (int m = 0; m < 32; ++m) if (m < P) x[m] = v;

@@ -173,9 +173,9 @@ __device__ void pass(const SweepArgs& A, const Smem2& S, double* s_red, const in
                     const float2 v = A.probe_z[(size_t)w * A.nz + e_row];
 #pragma unroll
                     for (int m = 0; m < 32; ++m)
-                        if (m < P) x[m] = A.probe_y ? cmul(v, __ldg(A.probe_y + t + T * m)) : v;
+                        if (m < P) x[m] = A.probe_y ? cmul(v, __ldg(A.probe_y + (size_t)w * ny + t + T * m)) : v;
                 } else {
-                    const float2 v = A.probe_y ? __ldg(A.probe_y + col) : make_float2(1.f, 0.f);
+                    const float2 v = A.probe_y ? __ldg(A.probe_y + (size_t)w * ny + col) : make_float2(1.f, 0.f);
 #pragma unroll
                     for (int m = 0; m < 32; ++m)
                         if (m < P) x[m] = cmul(__ldg(A.probe_z + (size_t)w * A.nz + t + T * m), v);

@@ -14,7 +14,7 @@ def params(geo, checkpoint_every=32, flags=0, schedule=0):
         flags |= B.MSLICE_ANGULAR
     return B.make_params(geo.ny, geo.nz, geo.ns, np.rad2deg(geo.alpha_i_rad), geo.wavelength_nm,
                          geo.slice_nm, geo.dy_nm, geo.dz_nm, checkpoint_every, flags, schedule=schedule,
-                         psi_rad=getattr(geo, "psi_rad", 0.0))
+                         psi_rad=getattr(geo, "psi_rad_w", 0.0))
 
 
 def dev(a, dtype):

@@ -75,6 +75,27 @@ def test_in_plane_angle_vs_oracle(psi_deg):
     assert G.rel(g, g_ref) <= TOL_GRAD
 
 
+@pytest.mark.parametrize("ny,nz,ns,K", [(128, 64, 20, 6), (64, 128, 13, 13)])
+def test_per_view_in_plane_angles_vs_oracle(ny, nz, ns, K):
+    """Several views, each with its own (alpha, psi) pair (Eq. 2-3 per view):
+    forward, loss and gradient summed over the views, against the oracle; and
+    each view's intensity equals the single-view call's."""
+    alphas, psis = (0.15, 0.3, 0.45, 0.25), (-0.5, 0.2, 0.0, 0.4)
+    geo = oracle.Geometry(ny, nz, ns, alpha_i_deg=alphas, psi_deg=psis)
+    vol = ci.random_volume(29 + ny, ny, nz, ns, scale=40)
+    I_ref = oracle.forward(geo, vol)
+    I = G.forward(geo, vol)
+    assert G.rel(I, I_ref) <= TOL_I
+    for w in range(len(alphas)):
+        g1 = oracle.Geometry(ny, nz, ns, alpha_i_deg=(alphas[w],), psi_deg=psis[w])
+        assert np.array_equal(G.forward(g1, vol)[0], I[w])
+    meas = (np.sqrt(I_ref) * 1.07).astype(np.float32)
+    L_ref, g_ref = oracle.loss_grad(geo, vol, meas, 0.9)
+    L, g = G.loss_grad(geo, vol, meas, 0.9, checkpoint_every=K)
+    assert abs(L - L_ref) <= 1e-4 * abs(L_ref)
+    assert G.rel(g, g_ref) <= TOL_GRAD
+
+
 def test_exact_transmission_fp64():
     """MSLICE_EXACT_TRANSMISSION: exp((k/2i) Delta (1 - n^2)), n = 1 - delta + i beta,
     evaluated in FP64 from n."""
@@ -436,7 +457,7 @@ def test_argument_errors():
         B.mslice_forward(p, vol, None, I, None, ws[: ws.numel() // 2])
     assert e.value.code == -5
     p2 = G.params(geo)
-    p2.psi_rad = 0.2                                # in-plane angle beyond the paraxial range
+    p2.psi_rad[0] = 0.2                             # in-plane angle beyond the paraxial range
     with pytest.raises(B.MsliceError) as e:
         B.mslice_forward(p2, vol, None, I, None, ws)
     assert e.value.code == -1

@@ -159,7 +159,7 @@ def measured_peaks():
         return {}
 
 
-SWEEP_SOURCES = ("mslice_device.cuh", "mslice_inst.cu", "mslice_kernels.h", "mslice_generic.cu")
+SWEEP_SOURCES = ("mslice_device.cuh", "mslice_slice.cuh", "mslice_inst.cu", "mslice_kernels.h", "mslice_generic.cu")
 
 
 def source_hash():

@@ -251,7 +251,8 @@ __device__ void pass(const SweepArgs& A, const Smem2& S, double* s_red, const in
                         if (active) {
                             // x = g_{a_j}: gradient -i kd a_j conj(g) (linearised) or with the
                             // factor (1 - conj(v)) (exact); the loads of a chunk of a_j are
-                            // issued before the chunk's stores
+                            // issued before the chunk's stores, and marked evict-first (a_j is
+                            // read once; the fields and gradient partials should stay in L2)
                             const float2* a = A.seg + (size_t)(j - A.seg_base) * nw * npx + fo;
                             float2* gdst = A.per_w ? (A.gradw[w] + (size_t)j * npx + e0)
                                            : (nw == 1 ? (A.grad + vo) : (A.gpart + (size_t)(j & 1) * nw * npx + fo));
@@ -261,7 +262,7 @@ __device__ void pass(const SweepArgs& A, const Smem2& S, double* s_red, const in
                                     float2 av[MS_ADJ_CHUNK];
 #pragma unroll
                                     for (int k = 0; k < MS_ADJ_CHUNK; ++k)
-                                        if (c0 + k < P) av[k] = __ldcg(a + (c0 + k) * es);
+                                        if (c0 + k < P) av[k] = __ldcs(a + (c0 + k) * es);
 #pragma unroll
                                     for (int k = 0; k < MS_ADJ_CHUNK; ++k) {
                                         if (c0 + k < P) {
@@ -280,7 +281,7 @@ __device__ void pass(const SweepArgs& A, const Smem2& S, double* s_red, const in
 #pragma unroll
                                     for (int k = 0; k < 8; ++k) {
                                         if (c0 + k < P) {
-                                            av[k] = __ldcg(a + (c0 + k) * es);
+                                            av[k] = __ldcs(a + (c0 + k) * es);
                                             vk[k] = __ldg(vv + (c0 + k) * es);
                                         }
                                     }
@@ -533,12 +534,25 @@ __global__ void __launch_bounds__(MS_THREADS, 1) k_slice_last(const SweepArgs A)
         if (!grid.sync()) return;
         const int ax = pass_axis(j) ^ 1;
         const int ntasks = ax == 0 ? A.nz * A.nw : ((A.ny + (1 << A.lcw) - 1) >> A.lcw) * A.nw;
-        if (threadIdx.x == 0) {
-            for (int w = blockIdx.x; w < A.nw; w += gridDim.x) {
-                double sum = 0.0;
-                for (int tk = w; tk < ntasks; tk += A.nw) sum += __ldcg(A.loss_task + tk);
-                A.loss_wsum[w] = sum;
-                if (A.per_w && A.lossw[w]) *A.lossw[w] = sum;
+        const int nper = (ntasks + A.nw - 1) / A.nw;   // tasks of one wavefield
+        for (int w = blockIdx.x; w < A.nw; w += gridDim.x) {   // uniform per block
+            // thread i sums tasks i, i + blockDim, ... of wavefield w in order, then
+            // a fixed tree over the threads (deterministic for the block size)
+            double sum = 0.0;
+            for (int i = threadIdx.x; i < nper; i += blockDim.x) {
+                const int tk = w + i * A.nw;
+                if (tk < ntasks) sum += __ldcg(A.loss_task + tk);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+            __syncthreads();
+            if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = sum;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                double tot = 0.0;
+                for (int i = 0; i < MS_WARPS; ++i) tot += s_red[i];
+                A.loss_wsum[w] = tot;
+                if (A.per_w && A.lossw[w]) *A.lossw[w] = tot;
             }
         }
         if (!grid.sync()) return;

@@ -399,10 +399,11 @@ int mslice_adam_step(float *theta, float *m, float *v, const float *grad, size_t
 int mslice_rotate(const mslice_params *p, double alpha_rad, double psi_rad, const double *center_nm,
                   const float *vol_sample, float *vol_lab, void *stream);
 
-/* g_sample = R^T g_lab (overwritten): the lab-frame gradient scattered back
- * with the interpolation weights.  Summed with float atomics, so the result
- * is not bitwise reproducible from run to run.  Buffers and errors as for
- * mslice_rotate. */
+/* g_sample = R^T g_lab (overwritten): the lab-frame gradient gathered back
+ * with the interpolation weights.  Every sample voxel sums the lab voxels
+ * whose stencils touch it in a fixed order, each stencil computed as
+ * mslice_rotate computes it, so the result is bitwise reproducible (no
+ * atomics).  Buffers and errors as for mslice_rotate. */
 int mslice_rotate_adjoint(const mslice_params *p, double alpha_rad, double psi_rad, const double *center_nm,
                           const float *g_lab, float *g_sample, void *stream);
 

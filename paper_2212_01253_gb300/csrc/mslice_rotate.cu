@@ -20,9 +20,11 @@
 // exact in FP32 for m < 2^12, and its fraction is taken exactly.  The weights
 // are then good to about 1e-7 absolute, at any volume size.
 //
-// Both kernels are bound by HBM: 8 B read (mostly from L2: neighbouring lab
-// voxels share sample voxels) and 8 B written per voxel.  The transpose
-// scatters with float atomics (its sums are not bitwise reproducible).
+// The forward is bound by HBM: 8 B read (mostly from L2: neighbouring lab
+// voxels share sample voxels) and 8 B written per voxel.  The transpose is a
+// gather: every sample voxel sums, in a fixed order, the lab voxels whose
+// stencils touch it, each stencil recomputed as the forward computes it, so
+// its result is bitwise reproducible (no atomics).
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -36,6 +38,10 @@ struct RotMap {
     double A[3][2];     // the row coefficients (j, l)
     float hi[3], lo[3]; // A[k][2] = hi + lo, hi with 12 significant bits
     int n[3];           // ns, nz, ny
+    float Af[3][3];     // A in FP32 (lab-index steps of the fractional sample index)
+    float C[3][3];      // A^-1 (sample-index steps of the lab index), for the gather's candidate box
+    float inv_ay;       // 1 / A[2][2] (0 when |A[2][2]| <= 1e-3: every lab column is a candidate)
+    int fmin[3], fmax[3];    // range of the fractional sample index over the lab volume (its corners)
 };
 
 // fraction-split index of one axis: lower lattice index and upper weight,
@@ -99,24 +105,9 @@ __device__ __forceinline__ float2 gather(const float2* __restrict__ in, const St
                        S.w000 * p00.y + S.w001 * p01.y + S.w100 * p10.y + S.w101 * p11.y);
 }
 
-__device__ __forceinline__ void scatter(float2* __restrict__ out, const Stencil& S, float2 g) {
-    float* dst = reinterpret_cast<float*>(out);
-    const size_t base[4] = {S.a00, S.a01, S.a10, S.a11};
-    const float wb[4] = {S.w000, S.w001, S.w100, S.w101};
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const float w0 = wb[q] * (1.f - S.wy), w1 = wb[q] * S.wy;
-        atomicAdd(dst + 2 * (base[q] + S.y0), w0 * g.x);
-        atomicAdd(dst + 2 * (base[q] + S.y0) + 1, w0 * g.y);
-        atomicAdd(dst + 2 * (base[q] + S.y1), w1 * g.x);
-        atomicAdd(dst + 2 * (base[q] + S.y1) + 1, w1 * g.y);
-    }
-}
-
 // one warp per lab row (j, l), lanes along y, two voxels per lane and step
 // (their loads in flight together).  Lanes 0..2 form the row's FP64 index
 // terms, one axis each, and pass them to the warp.
-template <bool ADJ>
 __global__ void __launch_bounds__(256) k_rotate(const float2* __restrict__ in, float2* __restrict__ out,
                                                 const RotMap R) {
     const int lane = threadIdx.x & 31;
@@ -148,15 +139,146 @@ __global__ void __launch_bounds__(256) k_rotate(const float2* __restrict__ in, f
             const bool two = m + 32 < ny;
             const Stencil S0 = stencil(R, ri, rf, m);
             const Stencil S1 = stencil(R, ri, rf, two ? m + 32 : m);
-            if constexpr (!ADJ) {
-                const float2 v0 = gather(in, S0);
-                const float2 v1 = gather(in, S1);
-                out[o + m] = v0;
-                if (two) out[o + m + 32] = v1;
-            } else {
-                scatter(out, S0, __ldg(in + o + m));
-                if (two) scatter(out, S1, __ldg(in + o + m + 32));
+            const float2 v0 = gather(in, S0);
+            const float2 v1 = gather(in, S1);
+            out[o + m] = v0;
+            if (two) out[o + m + 32] = v1;
+        }
+    }
+}
+
+// weight of sample index s in the stencil of lab column m along one axis:
+// axis_stencil's arithmetic with the indices kept as exact integers in FP32
+// (|index| < 2^24), so that no conversion is needed (ri, m, n, s as floats)
+__device__ __forceinline__ float axis_weight(float ri, float rf, float hi, float lo, float m, float n, float s) {
+    const float t = hi * m;
+    const float ti = floorf(t);
+    const float frac = rf + (t - ti) + lo * m;
+    const float fi = floorf(frac);
+    const float i = ri + ti + fi;
+    float w = frac - fi, i0 = i;
+    if (i < 0.f) {
+        i0 = 0.f;
+        w = 0.f;
+    } else if (i >= n - 1.f) {
+        i0 = n - 1.f;
+        w = 0.f;
+    }
+    const float i1 = i0 + 1.f < n ? i0 + 1.f : n - 1.f;
+    return (i0 == s ? 1.f - w : 0.f) + (i1 == s ? w : 0.f);
+}
+
+// lab-offset range [lo, hi] of one lab axis i reaching the sample window
+// D_k = [dlo_k, dhi_k] (infinite at the volume's faces) through C
+__device__ __forceinline__ void lab_range(const float (&C)[3], const float (&dlo)[3], const float (&dhi)[3],
+                                          float& lo, float& hi) {
+    lo = 0.f;
+    hi = 0.f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        if (C[k] == 0.f) continue;
+        const float a = C[k] * dlo[k], b = C[k] * dhi[k];
+        lo += fminf(a, b);
+        hi += fmaxf(a, b);
+    }
+}
+
+// Transpose R^T as a gather: one warp per sample row (x, z), lanes along y in
+// chunks of 32.  The lab row (x, z) is the reference: its FP64 index terms
+// are formed once, as the forward forms them, and a candidate lab row
+// (x + dx, z + dz) takes them plus FP32 offsets.  For each candidate lab voxel
+// the three axis stencils are computed as in the forward and the weight of
+// this sample voxel is its product; the candidates are visited in a fixed
+// order (dx, dz, then lab column), so the sum is bitwise reproducible.  The
+// candidate box is the lab image of the sample window [s - 1, s + 1] per axis
+// (at the volume's faces, where the forward clamps, out to the farthest index
+// a lab voxel reaches), with a tolerance of 1e-3 index units; the window's
+// offsets from the reference are integer differences plus the FP32 fraction,
+// so the tolerance holds at any volume size.
+__global__ void __launch_bounds__(256) k_rotate_gather(const float2* __restrict__ g_lab,
+                                                       float2* __restrict__ g_sample, const RotMap R) {
+    const int lane = threadIdx.x & 31;
+    const unsigned rows = (unsigned)R.n[0] * (unsigned)R.n[1];
+    const unsigned warps = gridDim.x * (blockDim.x >> 5);
+    const int ns = R.n[0], nz = R.n[1], ny = R.n[2];
+    for (unsigned row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); row < rows; row += warps) {
+        const int sx = (int)(row / (unsigned)nz), sz = (int)(row - (unsigned)sx * (unsigned)nz);
+        // reference lab row (sx, sz): integer and fraction of each axis's row term
+        int ri_k = 0;
+        float rf_k = 0.f;
+        if (lane < 3) {
+            const double b = lane == 0 ? R.b[0] : (lane == 1 ? R.b[1] : R.b[2]);
+            const double aj = lane == 0 ? R.A[0][0] : (lane == 1 ? R.A[1][0] : R.A[2][0]);
+            const double al = lane == 0 ? R.A[0][1] : (lane == 1 ? R.A[1][1] : R.A[2][1]);
+            const double f = fma(al, (double)sz, fma(aj, (double)sx, b));
+            const double fl = floor(f);
+            ri_k = (int)fl;
+            rf_k = (float)(f - fl);
+        }
+        int ri[3];
+        float rf[3], rif[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            ri[k] = __shfl_sync(0xffffffffu, ri_k, k);
+            rf[k] = __shfl_sync(0xffffffffu, rf_k, k);
+            rif[k] = (float)ri[k];
+        }
+        const float sxf = (float)sx, szf = (float)sz, nsf = (float)ns, nzf = (float)nz, nyf = (float)ny;
+        // sample window of the row, relative to the reference's row terms
+        // (integer difference, then the fraction)
+        const float dxlo = (float)((sx == 0 ? min(R.fmin[0], -1) : sx - 1) - ri[0]) - rf[0];
+        const float dxhi = (float)((sx == ns - 1 ? max(R.fmax[0], ns) : sx + 1) - ri[0]) - rf[0];
+        const float dzlo = (float)((sz == 0 ? min(R.fmin[1], -1) : sz - 1) - ri[1]) - rf[1];
+        const float dzhi = (float)((sz == nz - 1 ? max(R.fmax[1], nz) : sz + 1) - ri[1]) - rf[1];
+        const float tol = 1e-3f;
+        for (int c0 = 0; c0 < ny; c0 += 32) {
+            const int sy = c0 + lane;
+            const bool active = sy < ny;
+            const float syf = (float)sy;
+            const int ylast = c0 + 31 < ny - 1 ? c0 + 31 : ny - 1;
+            // the warp's candidate rows: the lab image of the chunk's window
+            const float dlo[3] = {dxlo, dzlo, (float)((c0 == 0 ? min(R.fmin[2], -1) : c0 - 1) - ri[2]) - rf[2]};
+            const float dhi[3] = {dxhi, dzhi, (float)((ylast == ny - 1 ? max(R.fmax[2], ny) : ylast + 1) - ri[2]) - rf[2]};
+            float xlo, xhi, zlo, zhi;
+            lab_range(R.C[0], dlo, dhi, xlo, xhi);
+            lab_range(R.C[1], dlo, dhi, zlo, zhi);
+            const int dx0 = (int)fmaxf(ceilf(xlo - tol), (float)-sx), dx1 = (int)fminf(floorf(xhi + tol), (float)(ns - 1 - sx));
+            const int dz0 = (int)fmaxf(ceilf(zlo - tol), (float)-sz), dz1 = (int)fminf(floorf(zhi + tol), (float)(nz - 1 - sz));
+            // this lane's window along y
+            const float ylo = (float)((sy == 0 ? min(R.fmin[2], -1) : sy - 1) - ri[2]) - rf[2];
+            const float yhi = (float)((sy == ny - 1 ? max(R.fmax[2], ny) : sy + 1) - ri[2]) - rf[2];
+            float2 acc = make_float2(0.f, 0.f);
+            for (int dx = dx0; dx <= dx1; ++dx) {
+                for (int dz = dz0; dz <= dz1; ++dz) {
+                    float rfc[3];
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) rfc[k] = rf[k] + R.Af[k][0] * (float)dx + R.Af[k][1] * (float)dz;
+                    if (!active) continue;
+                    // lab columns whose y index can reach sy: A_y2 m in the window less the row offset
+                    const float off = R.Af[2][0] * (float)dx + R.Af[2][1] * (float)dz;
+                    int m0 = 0, m1 = ny - 1;
+                    if (R.inv_ay != 0.f) {
+                        float a = (ylo - off) * R.inv_ay, b = (yhi - off) * R.inv_ay;
+                        if (a > b) { const float tmp = a; a = b; b = tmp; }
+                        m0 = (int)fmaxf(ceilf(a - tol), 0.f);
+                        m1 = (int)fminf(floorf(b + tol), (float)(ny - 1));
+                    }
+                    const float2* src = g_lab + ((size_t)(sx + dx) * nz + (size_t)(sz + dz)) * ny;
+                    float mf = (float)m0;
+                    for (int m = m0; m <= m1; ++m, mf += 1.f) {
+                        const float wy = axis_weight(rif[2], rfc[2], R.hi[2], R.lo[2], mf, nyf, syf);
+                        const float wx = axis_weight(rif[0], rfc[0], R.hi[0], R.lo[0], mf, nsf, sxf);
+                        const float wz = axis_weight(rif[1], rfc[1], R.hi[1], R.lo[1], mf, nzf, szf);
+                        const float wt = (wx * wz) * wy;
+                        // the load only where the voxel contributes (predicated, no branch)
+                        float2 g = make_float2(0.f, 0.f);
+                        if (wt != 0.f) g = __ldg(src + m);
+                        acc.x = fmaf(wt, g.x, acc.x);
+                        acc.y = fmaf(wt, g.y, acc.y);
+                    }
+                }
             }
+            if (active) g_sample[(size_t)row * ny + sy] = acc;
         }
     }
 }
@@ -198,17 +320,32 @@ int make_map(const mslice_params* p, double alpha, double psi, const double* c, 
     R->n[0] = p->ns;
     R->n[1] = p->nz;
     R->n[2] = p->ny;
+    R->inv_ay = fabs(M[2][2]) > 1e-3 ? (float)(1.0 / M[2][2]) : 0.f;   // A[2][2] = M[2][2]
+    // A (f per lab index) and its inverse C = S^-1 M S (M orthogonal): lab
+    // index per unit of f, S the spacings
+    for (int k = 0; k < 3; ++k)
+        for (int i = 0; i < 3; ++i) {
+            R->Af[k][i] = (float)(M[i][k] * sp3[i] / sp3[k]);
+            R->C[i][k] = (float)(M[i][k] * sp3[k] / sp3[i]);
+        }
     // the kernel keeps rows and lattice indices in 32 bits: the map is affine,
     // so its extremes over the volume are at the corners
     if ((double)p->ns * p->nz >= 2147483648.0) return MSLICE_EUNSUPPORTED;
-    for (int k = 0; k < 3; ++k)
+    for (int k = 0; k < 3; ++k) {
+        double lo = 0.0, hi = 0.0;
         for (int cj = 0; cj < 2; ++cj)
             for (int cl = 0; cl < 2; ++cl)
                 for (int cm = 0; cm < 2; ++cm) {
                     const double f = R->b[k] + R->A[k][0] * (cj ? p->ns - 1 : 0) + R->A[k][1] * (cl ? p->nz - 1 : 0) +
                                      ((double)R->hi[k] + R->lo[k]) * (cm ? p->ny - 1 : 0);
                     if (!(fabs(f) < 1073741824.0)) return MSLICE_EUNSUPPORTED;
+                    if ((cj | cl | cm) == 0 || f < lo) lo = f;
+                    if ((cj | cl | cm) == 0 || f > hi) hi = f;
                 }
+        // the gather's face windows reach the extreme index of the lab volume
+        R->fmin[k] = (int)floor(lo) - 1;
+        R->fmax[k] = (int)ceil(hi) + 1;
+    }
     return MSLICE_OK;
 }
 
@@ -228,15 +365,13 @@ int launch(const mslice_params* p, double alpha, double psi, const double* c, co
     if (rc) return rc;
     if (!in || !out || in == out || ((uintptr_t)in & 7) || ((uintptr_t)out & 7)) return MSLICE_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
-    const size_t n = (size_t)p->ns * p->nz * p->ny;
     const long long rows = (long long)p->ns * p->nz;
     const long long cap = (long long)device_sms() * 32;   // a few waves of 8-warp blocks per SM
     const unsigned blocks = (unsigned)(rows / 8 + 1 < cap ? rows / 8 + 1 : cap);
     if (adjoint) {
-        if (cudaMemsetAsync(out, 0, n * sizeof(float2), st) != cudaSuccess) return MSLICE_ELAUNCH;
-        k_rotate<true><<<blocks, 256, 0, st>>>((const float2*)in, (float2*)out, R);
+        k_rotate_gather<<<blocks, 256, 0, st>>>((const float2*)in, (float2*)out, R);
     } else {
-        k_rotate<false><<<blocks, 256, 0, st>>>((const float2*)in, (float2*)out, R);
+        k_rotate<<<blocks, 256, 0, st>>>((const float2*)in, (float2*)out, R);
     }
     return cudaGetLastError() == cudaSuccess ? MSLICE_OK : MSLICE_ELAUNCH;
 }

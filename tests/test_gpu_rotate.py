@@ -67,6 +67,27 @@ def test_rotate_adjoint_vs_oracle(shape, sp, alpha, psi, c, kind):
     assert G.rel(out.cpu().numpy(), ref) <= 1e-6
 
 
+def test_rotate_adjoint_is_bitwise_reproducible_and_a_transpose():
+    """The transpose is a gather in a fixed order: two calls agree bit for bit;
+    and <R x, y> = <x, R^T y> to FP32 rounding."""
+    from paper_2212_01253_gb300 import binding as B
+    shape, sp, alpha, psi, c, _ = CASES[0]
+    p = _params(*shape, sp)
+    g = G.dev(ci.random_volume(41, shape[2], shape[1], shape[0], scale=1.0), np.complex64)
+    x = G.dev(ci.random_volume(42, shape[2], shape[1], shape[0], scale=1.0), np.complex64)
+    a1 = torch.empty(shape, dtype=torch.complex64, device="cuda")
+    a2 = torch.empty_like(a1)
+    rx = torch.empty_like(a1)
+    B.mslice_rotate_adjoint(p, np.deg2rad(alpha), np.deg2rad(psi), c, g, a1)
+    B.mslice_rotate_adjoint(p, np.deg2rad(alpha), np.deg2rad(psi), c, g, a2)
+    B.mslice_rotate(p, np.deg2rad(alpha), np.deg2rad(psi), c, x, rx)
+    torch.cuda.synchronize()
+    assert torch.equal(a1, a2)
+    lhs = torch.vdot(rx.flatten().to(torch.complex128), g.flatten().to(torch.complex128))
+    rhs = torch.vdot(x.flatten().to(torch.complex128), a1.flatten().to(torch.complex128))
+    assert abs(complex(lhs) - complex(rhs)) <= 1e-6 * abs(complex(lhs))
+
+
 def test_zero_rotation_is_the_identity_bit_for_bit():
     from paper_2212_01253_gb300 import binding as B
     v = ci.random_volume(3, 48, 32, 10, scale=1.0)

@@ -86,10 +86,10 @@ extern "C" {
                                exp(i Delta (sqrt(k^2 - k_y^2 - k_z^2) - k)), and
                                exp(-Delta sqrt(k_perp^2 - k^2)) exp(-i Delta k)
                                for evanescent k_perp > k.  Not separable: the
-                               field is kept in (k_y, z) space between the row
-                               and column passes, and the run-time-size kernels
-                               run.  Not combined with MSLICE_EXIT_WAVE or
-                               MSLICE_STRANG (MSLICE_EUNSUPPORTED). */
+                               field is kept in (k_y, z) space between a row
+                               and a column pass per slice (two grid barriers
+                               per slice).  Not combined with MSLICE_EXIT_WAVE
+                               or MSLICE_STRANG (MSLICE_EUNSUPPORTED). */
 #define MSLICE_STRANG 8u  /* symmetric splitting of Eq. 1's slice step: half a
                              step of free propagation (Delta/2) before the first
                              slice; with MSLICE_EXIT_WAVE the last propagation is

@@ -54,8 +54,10 @@ def _units():
              (os.path.join(CSRC, "mslice_generic.cu"), os.path.join(BUILD_DIR, "generic_angular.o"),
               inc + ["-DMS_AS=1"])]
     for ny in ROW_LENGTHS:
-        units.append((os.path.join(CSRC, "mslice_inst.cu"), os.path.join(BUILD_DIR, "inst_ny%d.o" % ny),
-                      inc + ["-DMS_NY=%d" % ny]))
+        for a in (0, 1):   # paraxial one-pass / angular-spectrum two-pass instances
+            units.append((os.path.join(CSRC, "mslice_inst.cu"),
+                          os.path.join(BUILD_DIR, "inst_%sny%d.o" % ("as_" if a else "", ny)),
+                          inc + ["-DMS_NY=%d" % ny, "-DMS_AS=%d" % a]))
     return units
 
 

@@ -302,19 +302,18 @@ DevInfo g_dev[64];
 // an instance exists, generic otherwise) and the once-per-call kernels
 using KernelSet = ms_kernel_set;
 
-// the angular-spectrum propagator runs the run-time-size kernels with the
-// column pass on (k_y, k_z); the paraxial one the size-specialised instance
-// when there is one
+// the size-specialised instance when there is one (the angular spectrum: the
+// two-pass kernels with the column pass on (k_y, k_z)), else the run-time-size
+// kernels
 KernelSet sweep_kernels(int ny, int nz, bool angular) {
-    if (angular) return ms_generic_kernels_angular();
-    KernelSet ks = ms_generic_kernels_paraxial();
+    KernelSet ks = angular ? ms_generic_kernels_angular() : ms_generic_kernels_paraxial();
     ms_kernel_pair k{nullptr, nullptr};
     switch (ny) {
-        case 64: k = ms_sweep_kernels_ny64(nz); break;
-        case 128: k = ms_sweep_kernels_ny128(nz); break;
-        case 256: k = ms_sweep_kernels_ny256(nz); break;
-        case 512: k = ms_sweep_kernels_ny512(nz); break;
-        case 1024: k = ms_sweep_kernels_ny1024(nz); break;
+        case 64: k = angular ? ms_sweep_kernels_as_ny64(nz) : ms_sweep_kernels_ny64(nz); break;
+        case 128: k = angular ? ms_sweep_kernels_as_ny128(nz) : ms_sweep_kernels_ny128(nz); break;
+        case 256: k = angular ? ms_sweep_kernels_as_ny256(nz) : ms_sweep_kernels_ny256(nz); break;
+        case 512: k = angular ? ms_sweep_kernels_as_ny512(nz) : ms_sweep_kernels_ny512(nz); break;
+        case 1024: k = angular ? ms_sweep_kernels_as_ny1024(nz) : ms_sweep_kernels_ny1024(nz); break;
         default: break;
     }
     if (k.fwd && k.adj) {

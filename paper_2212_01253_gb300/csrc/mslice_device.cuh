@@ -719,10 +719,11 @@ __host__ __device__ __forceinline__ bool col_cw_ok(int cw, int T) {
 __host__ __device__ __forceinline__ int col_rs(int N, int cw) { return N + N / 32 + 16 / cw; }
 
 // ----- column pass: a group of cw*T threads per cw adjacent columns
-template <int OP, int NC = 0, bool AS = false>
+template <int OP, int NC = 0, bool AS = false, int NYC = 0>
 __device__ void col_pass(const SweepArgs& A, const Smem& S, double* s_red, const int w0 = 0, int wn = 0) {
     if (wn <= 0) wn = A.nw;
     const int N = NC ? NC : A.nz, T = row_T(N), P = N > 32 ? 32 : N;
+    const int NYr = NYC ? NYC : A.ny;   // row length: the column stride (compile-time when known)
     const int lcw = A.lcw, cw = 1 << lcw;
     const int lg = lcw + ilog2(T), gthreads = 1 << lg;
     const int groups = MS_THREADS >> lg;
@@ -730,7 +731,7 @@ __device__ void col_pass(const SweepArgs& A, const Smem& S, double* s_red, const
     const int c = gt & (cw - 1), t = gt >> lcw;
     float2* reg = S.exch + (size_t)(g * cw + c) * col_rs(N, cw);
     const size_t npx = (size_t)A.ny * A.nz;
-    const int ncg = (A.ny + cw - 1) / cw;
+    const int ncg = (NYr + cw - 1) / cw;
     const int ntasks = ncg * wn;
     const GroupSync sync{1 + g, gthreads};
     const float2* src = (OP == C_ADJ) ? A.gfield : (OP == C_SEED ? A.gpsi : A.field);
@@ -738,16 +739,16 @@ __device__ void col_pass(const SweepArgs& A, const Smem& S, double* s_red, const
     for (int task = blockIdx.x * groups + g; task < ntasks; task += gridDim.x * groups) {
         const int cg = task / wn, w = w0 + task % wn;
         const int col = cg * cw + c;
-        const bool active = col < A.ny;
-        const size_t base = (size_t)w * npx + col;
+        const bool active = col < NYr;
+        const size_t base = (size_t)w * ((size_t)NYr * N) + col;
         float2 x[32];
 #pragma unroll
         for (int m = 0; m < 32; ++m) {
             x[m] = make_float2(0.f, 0.f);
-            if (active && m < P) x[m] = __ldcg(src + base + (size_t)(t + T * m) * A.ny);
+            if (active && m < P) x[m] = __ldcg(src + base + (size_t)(t + T * m) * NYr);
         }
         if constexpr (OP == C_PROP || OP == C_EXIT || OP == C_ADJ) {
-            if constexpr (AS) propagate2d<OP == C_ADJ>(x, N, T, t, reg, S.Wz, A.p2d + col, A.ny, active, sync);
+            if constexpr (AS) propagate2d<OP == C_ADJ>(x, N, T, t, reg, S.Wz, A.p2d + col, NYr, active, sync);
             else propagate<OP == C_ADJ>(x, N, T, t, reg, S.Wz, S.Pz, sync);
         } else {
             if constexpr (OP != C_SEED) fft<false>(x, N, T, t, reg, S.Wz, sync);
@@ -757,7 +758,7 @@ __device__ void col_pass(const SweepArgs& A, const Smem& S, double* s_red, const
                     if (m < P) {
                         const float2 psi = cscale(x[m], A.ffz);
                         const float I = fmaf(psi.x, psi.x, psi.y * psi.y);
-                        const size_t o = base + (size_t)(t + T * m) * A.ny;
+                        const size_t o = base + (size_t)(t + T * m) * NYr;
                         if (active) {
                             if (A.intensity) __stcs(A.intensity + o, I);
                             if (A.field_out) __stcs(A.field_out + o, psi);
@@ -783,13 +784,13 @@ __device__ void col_pass(const SweepArgs& A, const Smem& S, double* s_red, const
         if constexpr (OP == C_SEED || OP == C_FAR_LOSS) {
 #pragma unroll
             for (int m = 0; m < 32; ++m)
-                if (m < P) __stcg(A.gfield + base + (size_t)(t + T * m) * A.ny, cscale(x[m], A.ffz));
+                if (m < P) __stcg(A.gfield + base + (size_t)(t + T * m) * NYr, cscale(x[m], A.ffz));
         } else {
             float2* dst = (OP == C_ADJ) ? A.gfield : A.field;
 #pragma unroll
             for (int m = 0; m < 32; ++m) {
                 if (m < P) {
-                    const size_t o = base + (size_t)(t + T * m) * A.ny;
+                    const size_t o = base + (size_t)(t + T * m) * NYr;
                     __stcg(dst + o, x[m]);
                     if constexpr (OP == C_EXIT) {
                         if (A.field_out) __stcs(A.field_out + o, x[m]);
@@ -906,7 +907,7 @@ __global__ void __launch_bounds__(MS_THREADS, 1) k_fwd_t(const SweepArgs A) {
                     for (int w = 0; w < (A.per_w ? A.nw : 1); ++w)
                         prefetch_l2(A.tvol + (size_t)w * A.ns * npx * A.per_w + (size_t)(j + 1) * npx, slice_bytes);
                 }
-                col_pass<C_PROP, NZ, AS>(A, S, s_red);
+                col_pass<C_PROP, NZ, AS, NY>(A, S, s_red);
                 if (j < A.j_end - 1 && !grid.sync()) return;
             }
         }
@@ -939,7 +940,7 @@ __global__ void __launch_bounds__(MS_THREADS, 1) k_fwd_t(const SweepArgs A) {
 #pragma unroll
         for (int g = 0; g < 2; ++g) {
             if (!grid.wait(slot[g], arr[g])) return;                       // R_g(j) done
-            col_pass<C_PROP, NZ, AS>(A, S, s_red, gw0[g], gwn[g]);
+            col_pass<C_PROP, NZ, AS, NY>(A, S, s_red, gw0[g], gwn[g]);
             if (j < A.j_end - 1) {
                 grid.arrive(slot[g]);
                 ++arr[g];
@@ -1000,7 +1001,7 @@ __global__ void __launch_bounds__(MS_THREADS, 1) k_adj_t(const SweepArgs A) {
                                 npx * sizeof(float2));
                 prefetch_l2(A.seg + (size_t)(j - 1 - A.seg_base) * A.nw * npx, A.nw * npx * sizeof(float2));
             }
-            if (j > 0) col_pass<C_ADJ, NZ, AS>(A, S, s_red);
+            if (j > 0) col_pass<C_ADJ, NZ, AS, NY>(A, S, s_red);
             if (reduce) reduce_gpart(A, j);
             if (j > A.j_begin && !grid.sync()) return;
         }
@@ -1030,7 +1031,7 @@ __global__ void __launch_bounds__(MS_THREADS, 1) k_adj_t(const SweepArgs A) {
 #pragma unroll
         for (int g = 0; g < 2; ++g) {
             if (!grid.wait(slot[g], arr[g])) return;                        // R_g(j) done
-            if (j > 0) col_pass<C_ADJ, NZ, AS>(A, S, s_red, gw0[g], gwn[g]);
+            if (j > 0) col_pass<C_ADJ, NZ, AS, NY>(A, S, s_red, gw0[g], gwn[g]);
             if (g == 1 && reduce) reduce_gpart(A, j);
             if (j > A.j_begin) {
                 grid.arrive(slot[g]);

@@ -1,8 +1,9 @@
 // mslice_kernels.h -- the slice-loop kernels, instantiated in translation
 // units of their own so that they compile in parallel:
-//   mslice_inst.cu (one unit per row length ny, -DMS_NY=ny): size-specialised
-//     one-pass forward and adjoint kernels for each column length nz, or null
-//     pointers if that pair has no specialised instance;
+//   mslice_inst.cu (one unit per row length ny and propagator, -DMS_NY=ny
+//     -DMS_AS=0/1): size-specialised forward and adjoint kernels for each
+//     column length nz (one-pass paraxial, or two-pass angular spectrum), or
+//     null pointers if that pair has no specialised instance;
 //   mslice_generic.cu (-DMS_AS=0 and -DMS_AS=1): the run-time-size kernels and
 //     the once-per-call kernels, for the paraxial propagator and for the
 //     angular spectrum.
@@ -18,6 +19,12 @@ ms_kernel_pair ms_sweep_kernels_ny128(int nz);
 ms_kernel_pair ms_sweep_kernels_ny256(int nz);
 ms_kernel_pair ms_sweep_kernels_ny512(int nz);
 ms_kernel_pair ms_sweep_kernels_ny1024(int nz);
+// the same for the angular-spectrum propagator (two-pass kernels)
+ms_kernel_pair ms_sweep_kernels_as_ny64(int nz);
+ms_kernel_pair ms_sweep_kernels_as_ny128(int nz);
+ms_kernel_pair ms_sweep_kernels_as_ny256(int nz);
+ms_kernel_pair ms_sweep_kernels_as_ny512(int nz);
+ms_kernel_pair ms_sweep_kernels_as_ny1024(int nz);
 
 struct ms_kernel_set {
     const void* fwd;             // k_slice_fwd (one pass per slice) or k_fwd_t (two)

@@ -88,8 +88,9 @@ extern "C" {
                                for evanescent k_perp > k.  Not separable: the
                                field is kept in (k_y, z) space between a row
                                and a column pass per slice (two grid barriers
-                               per slice).  Not combined with MSLICE_EXIT_WAVE
-                               or MSLICE_STRANG (MSLICE_EUNSUPPORTED). */
+                               per slice).  Combines with MSLICE_EXIT_WAVE and
+                               MSLICE_STRANG (half steps over Delta/2 of the
+                               same propagator). */
 #define MSLICE_STRANG 8u  /* symmetric splitting of Eq. 1's slice step: half a
                              step of free propagation (Delta/2) before the first
                              slice; with MSLICE_EXIT_WAVE the last propagation is

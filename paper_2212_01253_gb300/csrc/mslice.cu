@@ -215,7 +215,6 @@ int validate(const mslice_params* p) {
     if (p->flags & ~(MSLICE_EXIT_WAVE | MSLICE_PER_STRUCTURE | MSLICE_EXACT_TRANSMISSION | MSLICE_STRANG |
                      MSLICE_ANGULAR))
         return MSLICE_EINVAL;
-    if ((p->flags & MSLICE_ANGULAR) && (p->flags & (MSLICE_EXIT_WAVE | MSLICE_STRANG))) return MSLICE_EUNSUPPORTED;
     if (p->grid_blocks < 0 || p->col_width < 0 || p->schedule < 0 || p->schedule > 2) return MSLICE_EINVAL;
     if (p->col_width > 0 && !col_cw_ok(p->col_width, p->nz > 32 ? p->nz / 32 : 1)) return MSLICE_EINVAL;
     return MSLICE_OK;
@@ -225,6 +224,7 @@ struct Layout {
     size_t ctrl, partials, tab, probe_z, probe_y, tvol, field, gfield, gpart, ckpt, seg;
     size_t tab_half, probe_half, zero_t;  // symmetric splitting only (0 otherwise)
     size_t p2d;                           // angular spectrum only (0 otherwise)
+    size_t p2d_half;                      // angular spectrum with the symmetric splitting
     size_t loss_task, loss_wsum;          // one-pass loss partials (loss + gradient)
     size_t total;
     int K, nseg;
@@ -248,6 +248,9 @@ Layout make_layout(const mslice_params* p, int op) {
     L.field = off; off = align256(off + fb);
     if (p->flags & MSLICE_ANGULAR) {
         L.p2d = off; off = align256(off + npx * sizeof(float2));
+        if (p->flags & MSLICE_STRANG) {
+            L.p2d_half = off; off = align256(off + npx * sizeof(float2));
+        }
     }
     if (p->flags & MSLICE_STRANG) {
         L.tab_half = off; off = align256(off + 2 * (size_t)(p->ny + p->nz) * sizeof(float2));
@@ -508,6 +511,7 @@ struct Plan {
     int grid;
     SweepArgs base;
     const float2* tab_half;  // P over Delta/2 (symmetric splitting), else null
+    const float2* p2d_half;  // the angular spectrum's 2-D table over Delta/2, else null
 };
 
 // jt: per-structure buffers (per-structure runs: the transmission of each
@@ -615,12 +619,20 @@ int prepare(const mslice_params* p, int op, const float* vol, const float* probe
     a.per_w = (p->flags & MSLICE_PER_STRUCTURE) ? 1 : 0;
     a.lcw = ilog2(cw);
     a.split = p->nw >= 2 && p->schedule == 2;
+    P->p2d_half = nullptr;
     if (p->flags & MSLICE_ANGULAR) {
         const size_t n2 = (size_t)p->ny * p->nz;
-        k_setup_p2d<<<(unsigned)((n2 + 255) / 256 < 4096 ? (n2 + 255) / 256 : 4096), 256, 0, st>>>(
-            (float2*)(w + L.p2d), p->ny, p->nz, p->dy_nm, p->dz_nm, p->slice_nm, p->wavelength_nm);
+        const unsigned blocks = (unsigned)((n2 + 255) / 256 < 4096 ? (n2 + 255) / 256 : 4096);
+        k_setup_p2d<<<blocks, 256, 0, st>>>((float2*)(w + L.p2d), p->ny, p->nz, p->dy_nm, p->dz_nm, p->slice_nm,
+                                            p->wavelength_nm);
         if (note(cudaGetLastError(), "k_setup_p2d launch")) return MSLICE_ELAUNCH;
         a.p2d = (const float2*)(w + L.p2d);
+        if (strang) {
+            k_setup_p2d<<<blocks, 256, 0, st>>>((float2*)(w + L.p2d_half), p->ny, p->nz, p->dy_nm, p->dz_nm,
+                                                0.5 * p->slice_nm, p->wavelength_nm);
+            if (note(cudaGetLastError(), "k_setup_p2d launch")) return MSLICE_ELAUNCH;
+            P->p2d_half = (const float2*)(w + L.p2d_half);
+        }
     }
     P->tab_half = nullptr;
     if (strang) {
@@ -639,9 +651,17 @@ int prepare(const mslice_params* p, int op, const float* vol, const float* probe
         h.j_begin = 0; h.j_end = 1;
         h.prop_last = 1;
         h.flags = P->ks.one_pass ? F_PROP_FULL : 0;   // both axes' factors
+        if (P->p2d_half) {
+            // angular spectrum: the half step leaves (k_y, z) data in the field
+            // buffer, which the first slice of the forward takes as the output
+            // of a previous slice (its row pass transforms back to real space)
+            h.p2d = P->p2d_half;
+            h.field = (float2*)(w + L.field);
+        }
         rc = launch_coop(P->ks.fwd, P->grid, P->smem, h, st, KID_FWD, (double)p->nw * p->ny * p->nz);
         if (rc) return rc;
-        a.probe = (const float2*)(w + L.probe_half);
+        if (P->p2d_half) a.field_start = 1;
+        else a.probe = (const float2*)(w + L.probe_half);
     }
     return MSLICE_OK;
 }
@@ -685,6 +705,7 @@ int run_gradient(const mslice_params* p, Plan& P, bool loss, cudaStream_t st) {
             f.j_begin = j0; f.j_end = j1;
             f.prop_last = 0;
             f.init_ckpt = s;
+            f.field_start = 0;
             f.seg_base = j0; f.seg_from = j0;
             if ((rc = launch_coop(P.ks.fwd, P.grid, P.smem, f, st, KID_FWD, u * (j1 - j0 - 1)))) return rc;
         }
@@ -717,6 +738,7 @@ int run_forward(const mslice_params* p, Plan& P, float* intensity, float* field_
         // the last transmission; slice ns-2's second factor is a full step)
         if (P.tab_half) {
             if (P.ks.one_pass) a.tab2 = P.tab_half;
+            else if (P.p2d_half) a.p2d = P.p2d_half;   // angular spectrum: the last column pass
             else a.tab = P.tab_half;
         }
         return launch_coop(P.ks.last_exit, P.grid, P.smem, a, st, KID_LAST, u);

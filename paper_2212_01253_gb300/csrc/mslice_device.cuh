@@ -475,6 +475,9 @@ struct SweepArgs {
     const float2* p2d;      // [nz][ny] angular-spectrum propagator / (ny nz) (AS kernels only)
     const float2* tab2;     // one-pass kernels: table whose P parts serve the last slice's
                             // post-transmission propagation (half steps), or null
+    int field_start;        // two-pass kernels: the first slice of the launch reads `field` as the
+                            // output of a previous slice ((k_y, z) data with the angular spectrum:
+                            // the half-stepped probe of the symmetric splitting)
     double* loss_task;      // one-pass loss: FP64 partial of every task of the detector pass
     double* loss_wsum;      // one-pass loss: per-wavefield sums [nw]
     float scales[MSLICE_MAX_ANGLES];  // per-wavefield loss scale when per_w
@@ -509,6 +512,7 @@ enum : int {
     R_FAR = 1,       // a = t_j phi; [seg store]; F_y / sqrt(ny)           -> field
     R_ADJ = 2,       // grad_j from a_j, g; [g <- F^-1 conj(P_y) F conj(t_j) g] -> gfield
     R_ADJ_FAR = 3,   // g <- F_y^H g (unitary)                             -> gfield
+    R_EXIT = 4,      // AS: back from (k_y, z): phi_Ns, |phi_Ns|^2         field -> outputs
 };
 // column-pass operations
 enum : int {
@@ -687,6 +691,24 @@ __device__ void row_pass(const SweepArgs& A, const Smem& S, const int j, const b
             if (active) {
 #pragma unroll
                 for (int m = 0; m < 32; ++m) if (m < P) __stcg(A.gfield + row + t + T * m, x[m]);
+            }
+        } else if constexpr (OP == R_EXIT) {
+            // the exit wave of the angular-spectrum loop: the last column pass
+            // left (k_y, z) data scaled by 1/ny; the unnormalised inverse
+            // y-transform returns phi_Ns
+            if (active) {
+#pragma unroll
+                for (int m = 0; m < 32; ++m) if (m < P) x[m] = __ldcg(A.field + row + t + T * m);
+            }
+            fft<true>(x, N, T, t, reg, S.Wy, sync);
+            if (active) {
+#pragma unroll
+                for (int m = 0; m < 32; ++m) {
+                    if (m < P) {
+                        if (A.field_out) __stcs(A.field_out + row + t + T * m, x[m]);
+                        if (A.intensity) __stcs(A.intensity + row + t + T * m, fmaf(x[m].x, x[m].x, x[m].y * x[m].y));
+                    }
+                }
             }
         } else {  // R_ADJ_FAR
             if (active) {
@@ -900,7 +922,7 @@ __global__ void __launch_bounds__(MS_THREADS, 1) k_fwd_t(const SweepArgs A) {
     if (!A.split) {
         for (int j = A.j_begin; j < A.j_end; ++j) {
             const bool prop = (j < A.j_end - 1) || A.prop_last;
-            row_pass<R_FWD, NY, AS>(A, S, j, j == A.j_begin, prop);
+            row_pass<R_FWD, NY, AS>(A, S, j, j == A.j_begin && !A.field_start, prop);
             if (prop) {
                 if (!grid.sync()) return;
                 if (j + 1 < A.j_end) {
@@ -926,7 +948,7 @@ __global__ void __launch_bounds__(MS_THREADS, 1) k_fwd_t(const SweepArgs A) {
 #pragma unroll
         for (int g = 0; g < 2; ++g) {
             if (j > A.j_begin && !grid.wait(slot[g], arr[g])) return;   // C_g(j-1) done
-            row_pass<R_FWD, NY, AS>(A, S, j, j == A.j_begin, prop, gw0[g], gwn[g]);
+            row_pass<R_FWD, NY, AS>(A, S, j, j == A.j_begin && !A.field_start, prop, gw0[g], gwn[g]);
             if (prop) {
                 grid.arrive(slot[g]);
                 ++arr[g];
@@ -955,10 +977,18 @@ template <int COL, bool AS = false>
 __global__ void __launch_bounds__(MS_THREADS, 1) k_last(const SweepArgs A) {
     MS_KERNEL_PROLOGUE
     const int j = A.ns - 1;
-    if constexpr (COL == C_EXIT) row_pass<R_FWD, 0, AS>(A, S, j, j == A.j_begin, true);
-    else row_pass<R_FAR, 0, AS>(A, S, j, j == A.j_begin, true);
+    const bool first = j == A.j_begin && !A.field_start;
+    if constexpr (COL == C_EXIT) row_pass<R_FWD, 0, AS>(A, S, j, first, true);
+    else row_pass<R_FAR, 0, AS>(A, S, j, first, true);
     if (!grid.sync()) return;
-    col_pass<COL, 0, AS>(A, S, s_red);
+    if constexpr (COL == C_EXIT && AS) {
+        // angular spectrum: propagate on (k_y, k_z), then back to real space
+        col_pass<C_PROP, 0, AS>(A, S, s_red);
+        if (!grid.sync()) return;
+        row_pass<R_EXIT, 0, AS>(A, S, j, false, true);
+    } else {
+        col_pass<COL, 0, AS>(A, S, s_red);
+    }
     if constexpr (COL == C_FAR_LOSS) {
         if (!grid.sync()) return;
         if (blockIdx.x == 0 && threadIdx.x == 0) {

@@ -13,8 +13,8 @@
 #if MS_AS
 ms_kernel_set ms_generic_kernels_angular() {
     return {(const void*)k_fwd_t<0, 0, true>, (const void*)k_adj_t<0, 0, true>, (const void*)k_last<C_FAR, true>,
-            (const void*)k_last<C_FAR_LOSS, true>, nullptr, (const void*)k_adj_start<true, true>,
-            (const void*)k_adj_start<false, true>, 0};
+            (const void*)k_last<C_FAR_LOSS, true>, (const void*)k_last<C_EXIT, true>,
+            (const void*)k_adj_start<true, true>, (const void*)k_adj_start<false, true>, 0};
 }
 #else
 ms_kernel_set ms_generic_kernels_paraxial() {

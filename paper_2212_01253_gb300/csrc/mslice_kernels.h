@@ -31,7 +31,7 @@ struct ms_kernel_set {
     const void* adj;             // k_slice_adj or k_adj_t
     const void* last_far;        // k_slice_last<P_FAR> or k_last<C_FAR>
     const void* last_loss;       // k_slice_last<P_FAR_LOSS> or k_last<C_FAR_LOSS>
-    const void* last_exit;       // k_slice_last<P_EXIT> (null with the angular spectrum)
+    const void* last_exit;       // k_slice_last<P_EXIT> or k_last<C_EXIT>
     const void* adj_start_seed;  // k_slice_seed or k_adj_start<true>
     const void* adj_start;       // k_adj_start<false> (two-pass kernels only, else null)
     int one_pass;                // 1: one pass per slice, alternating axes (paraxial);

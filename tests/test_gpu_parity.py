@@ -269,18 +269,38 @@ def test_option_combinations_loss_grad_vs_oracle(opts):
     assert G.rel(g, g_ref) <= TOL_GRAD
 
 
-def test_angular_rejects_exit_wave_and_strang():
-    from paper_2212_01253_gb300 import binding as B
-    for extra in (B.MSLICE_EXIT_WAVE, B.MSLICE_STRANG):
-        p = B.make_params(32, 32, 4, (0.3,), flags=B.MSLICE_ANGULAR | extra)
-        assert B._load().mslice_workspace_size(p, B.MSLICE_OP_FORWARD) == 0
-        ws = torch.empty(1 << 20, dtype=torch.uint8, device="cuda")
-        I = torch.empty((1, 32, 32), dtype=torch.float32, device="cuda")
-        F = torch.empty((1, 32, 32), dtype=torch.complex64, device="cuda")
-        v = torch.zeros((4, 32, 32), dtype=torch.complex64, device="cuda")
-        with pytest.raises(B.MsliceError) as e:
-            B.mslice_forward(p, v, None, I, F, ws)
-        assert e.value.code == -2
+@pytest.mark.parametrize("ny,nz,ns,nw,K,schedule", [(64, 64, 12, 2, 5, 0), (32, 64, 9, 3, 4, 2),
+                                                    (64, 128, 1, 2, 1, 0)])
+def test_angular_with_symmetric_splitting_vs_oracle(ny, nz, ns, nw, K, schedule):
+    """Angular spectrum and the symmetric splitting together: the half step
+    before the first slice is the angular-spectrum propagator over Delta/2;
+    forward, loss and gradient (checkpointed), one slice included."""
+    geo = oracle.Geometry(ny, nz, ns, dy_nm=1.0, dz_nm=1.0, alpha_i_deg=np.linspace(0.15, 0.45, nw),
+                          angular=True, strang=True, psi_deg=0.3)
+    vol = ci.random_volume(5 * ny + ns, ny, nz, ns, scale=60)
+    I_ref = oracle.forward(geo, vol)
+    assert G.rel(G.forward(geo, vol, schedule=schedule), I_ref) <= TOL_I
+    meas = _target(geo, vol.astype(np.complex128) * 1.1, 8)
+    L_ref, g_ref, I2 = oracle.loss_grad(geo, vol, meas, 0.7, return_intensity=True)
+    L, g, I = G.loss_grad(geo, vol, meas, 0.7, checkpoint_every=K, return_intensity=True, schedule=schedule)
+    assert G.rel(I, I2) <= TOL_I
+    assert abs(L - L_ref) <= 1e-4 * abs(L_ref)
+    assert G.rel(g, g_ref) <= TOL_GRAD
+
+
+@pytest.mark.parametrize("strang", [False, True])
+@pytest.mark.parametrize("ny,nz,ns", [(64, 64, 10), (128, 64, 1)])
+def test_angular_exit_wave_vs_oracle(ny, nz, ns, strang):
+    """The exit wave phi_Ns with the angular spectrum (back from (k_y, z) after
+    the last propagation; a half step with the symmetric splitting), user probe
+    and default probe."""
+    geo = oracle.Geometry(ny, nz, ns, dy_nm=1.0, dz_nm=1.0, alpha_i_deg=(0.2, 0.35), angular=True,
+                          strang=strang)
+    vol = ci.random_volume(9 * ny + ns, ny, nz, ns, scale=60)
+    for probe in (None, ci.random_probe(ny + nz, 2, ny, nz)):
+        ref = oracle.forward(geo, vol, probe=probe, exit_wave=True)
+        got = G.forward(geo, vol, probe=probe, exit_wave=True)
+        assert G.rel(got, ref) <= TOL_I
 
 
 # --------------------------------------------------------------------------

@@ -491,7 +491,19 @@ def run_batch(args):
                          alpha_deg=sp["alpha_deg"]))
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t0
-    bat = BatchedLossGrad(jobs, tune=not args.no_tune, lanes=args.lanes)
+    # checkpoint interval as for the headline: --checkpoint if given, else
+    # every a_j kept (one segment per group, no recompute) when the batch's
+    # workspace fits in half of the device's memory, else every 32 slices
+    ckpt = args.checkpoint if args.checkpoint > 0 else 1 << 30
+    if args.checkpoint <= 0:
+        probe_jobs = B.make_jobs([dict(vol=jb["vol"], alpha_deg=jb["alpha_deg"], meas=jb["meas"], scale=1.0,
+                                       grad=jb["vol"]) for jb in jobs])
+        need = B.mslice_batched_workspace_size(B.make_params(64, 64, 1, checkpoint_every=ckpt), probe_jobs,
+                                               B.MSLICE_OP_LOSS_GRAD, args.lanes)
+        free, _ = torch.cuda.mem_get_info(dev)
+        if need + sum(jb["vol"].numel() * 8 for jb in jobs) > free // 2:
+            ckpt = CKPT
+    bat = BatchedLossGrad(jobs, tune=not args.no_tune, lanes=args.lanes, checkpoint_every=ckpt)
     bat.capture()
     for _ in range(args.warmup):
         bat.replay()
@@ -525,6 +537,7 @@ def run_batch(args):
             "dtype": "f32", "data": "synthetic",
             "config": {"workload": "%d structures, grids 128-512 per axis, 128-1024 slices, 0.1-0.5 deg, "
                                    "one CUDA graph per rank" % len(all_specs),
+                       "checkpoint": "every a_j kept" if ckpt > 1024 else "every %d slices" % ckpt,
                        "structures_rank0": len(jobs), "groups_rank0": bat.ngroups, "lanes": bat.lanes,
                        "api": "mslice_loss_grad_batched (one C call: grouping, lanes and launch sequences "
                               "in the library)",
@@ -1001,7 +1014,8 @@ def main():
     ap.add_argument("--checkpoint", type=int, default=0,
                     help="adjoint checkpoint interval (0: keep every a_j when it fits in half the HBM, else 32)")
     ap.add_argument("--jobs", type=int, default=64)
-    ap.add_argument("--lanes", type=int, default=4, help="batch: concurrent streams, SMs split between them")
+    ap.add_argument("--lanes", type=int, default=16,
+                    help="batch: concurrent lanes (each group's kernels on the blocks its tasks need)")
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--no-ckpt32", action="store_true", help="sweep: skip the checkpoint-every-32 leg")
     ap.add_argument("--no-recon", action="store_true", help="sweep: skip the reconstruction leg")

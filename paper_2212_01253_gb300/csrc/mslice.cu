@@ -781,7 +781,21 @@ mslice_params group_params(const mslice_params* common, const mslice_job* jobs, 
     q.flags |= MSLICE_PER_STRUCTURE;
     const int cw = jobs[g.idx[0]].col_width;
     if (cw > 0) q.col_width = cw;
-    if (lanes > 1) q.grid_blocks = sms / lanes > 0 ? sms / lanes : 1;
+    if (lanes > 1) {
+        // concurrent lanes: each group's persistent kernels on the blocks its
+        // tasks need (about two row or column tasks per warp or group and
+        // pass), at most SMs / 2, so that small groups (whose slice loops are
+        // bound by barrier latency) hold few SMs and many run at once
+        const int Ty = q.ny > 32 ? q.ny / 32 : 1, Tz = q.nz > 32 ? q.nz / 32 : 1;
+        const int cwq = col_width(&q);
+        const long row_tasks = (long)q.nz * q.nw, row_per_block = MS_THREADS / Ty;
+        const long col_tasks = (long)((q.ny + cwq - 1) / cwq) * q.nw, col_per_block = MS_THREADS / (cwq * Tz);
+        long need = (row_tasks + 2 * row_per_block - 1) / (2 * row_per_block);
+        const long need_c = (col_tasks + 2 * col_per_block - 1) / (2 * col_per_block);
+        if (need_c > need) need = need_c;
+        const long cap = sms / 2 > 0 ? sms / 2 : 1;
+        q.grid_blocks = (int)(need < 1 ? 1 : (need > cap ? cap : need));
+    }
     return q;
 }
 
@@ -822,8 +836,11 @@ int plan_batch(const mslice_params* common, const mslice_job* jobs, int njobs, i
         g.ws_off = off;
         g.ws_bytes = make_layout(&q, op).total;
         off = align256(off + g.ws_bytes);
-        // work plus a per-slice latency term (grid barriers of latency-bound slice steps)
-        g.cost = (double)g.n * g.ny * g.nz * g.ns / 4e10 + g.ns * 2.5e-5;
+        // wall time of the group on its blocks: its work at the rate of those
+        // blocks (5e10 units/s on the whole GPU) plus a per-slice latency term
+        // (the grid barriers of latency-bound slice steps)
+        const double blocks = q.grid_blocks > 0 ? q.grid_blocks : sms;
+        g.cost = (double)g.n * g.ny * g.nz * g.ns / (5e10 * blocks / sms) + g.ns * 2.5e-5;
         order[k] = (int)k;
     }
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return G[a].cost > G[b].cost; });

@@ -439,6 +439,12 @@ def run_gpu(args):
             "gpu_launches": gpu_launches, "kernels": kernels, "loss": float(loss.item()),
             "checkpoint32": ck32,
             "recon": None if (args.no_recon or world > 1) else recon_leg(args, dev)}
+    if not args.no_batch and world == 1:
+        bl = batch_measure(args, dev)
+        bl["of_headline"] = bl["value"] / value
+        line["batch"] = bl
+    else:
+        line["batch"] = None
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -448,32 +454,18 @@ def run_gpu(args):
 # ---------------------------------------------------------------------------
 # extra workloads (not the headline line): batched uneven jobs, reconstruction
 # ---------------------------------------------------------------------------
-def run_batch(args):
-    """64 independent structures of uneven shape (grids 128..512 per axis,
-    128..1024 slices, 0.1-0.5 deg), loss + gradient of all of them as one
-    CUDA-graph launch; voxel-slice-steps/s over the whole batch.  Under
-    torchrun the structures are split between the ranks by index (strong
-    scaling: the batch is fixed)."""
+def batch_measure(args, dev, world=1, rank=0):
+    """Loss + gradient of the 64 uneven structures (this rank's share of
+    them) as one CUDA-graph replay of mslice_loss_grad_batched; returns the
+    whole-job rate and the details of the run."""
     import torch
     import torch.distributed as dist
 
     import cssi_inputs as ci
     from paper_2212_01253_gb300 import binding as B
-    from paper_2212_01253_gb300 import build as cuda_build
     from paper_2212_01253_gb300.batch import BatchedLossGrad
     from paper_2212_01253_gb300.shard import shard, whole_job_rate
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    if world > 1:
-        dist.init_process_group("nccl", device_id=dev)
-    if rank == 0 or not os.path.exists(cuda_build.LIB):
-        cuda_build.build()
-    if world > 1:
-        dist.barrier()
     all_specs = ci.batched_jobs(0, args.jobs)
     specs = [all_specs[i] for i in shard(len(all_specs), rank, world)]
     jobs = []
@@ -481,10 +473,10 @@ def run_batch(args):
     for k, sp in enumerate(specs):
         ny, nz, ns = sp["ny"], sp["nz"], sp["ns"]
         vol = torch.from_numpy(ci.pillars_large(sp["seed"] % (1 << 20), ny=ny, nz=nz, ns=ns,
-                                                count=max(4, ny * ns // 10000))).cuda()
+                                                count=max(4, ny * ns // 10000))).to(dev)
         p = B.make_params(ny, nz, ns, (sp["alpha_deg"],))
         ws = B.workspace(p, B.MSLICE_OP_FORWARD)
-        inten = torch.empty((1, nz, ny), dtype=torch.float32, device="cuda")
+        inten = torch.empty((1, nz, ny), dtype=torch.float32, device=dev)
         B.mslice_forward(p, vol, None, inten, None, ws)
         del ws
         jobs.append(dict(vol=vol, meas=torch.sqrt(inten[0] * 1.05).contiguous(), scale=1.0,
@@ -503,7 +495,7 @@ def run_batch(args):
         free, _ = torch.cuda.mem_get_info(dev)
         if need + sum(jb["vol"].numel() * 8 for jb in jobs) > free // 2:
             ckpt = CKPT
-    bat = BatchedLossGrad(jobs, tune=not args.no_tune, lanes=args.lanes, checkpoint_every=ckpt)
+    bat = BatchedLossGrad(jobs, tune=not args.no_tune, lanes=args.lanes, checkpoint_every=ckpt, device=dev)
     bat.capture()
     for _ in range(args.warmup):
         bat.replay()
@@ -520,28 +512,58 @@ def run_batch(args):
         dist.barrier()
     bat.check()
     value, ms = whole_job_rate(bat.units, e0.elapsed_time(e1) / args.steps, dev)
-    # the same batch as eager per-group calls (no graph) for comparison
+    # the same batch as eager calls (no graph) for comparison
     f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     f0.record()
     for _ in range(args.steps):
         bat.run()
     f1.record()
     torch.cuda.synchronize()
-    eager_ms = f0.elapsed_time(f1) / args.steps
+    out = {"value": value, "unit": UNIT, "ms_per_step": ms, "eager_ms_per_step": f0.elapsed_time(f1) / args.steps,
+           "workload": "%d structures, grids 128-512 per axis, 128-1024 slices, 0.1-0.5 deg, one CUDA graph "
+                       "per rank" % len(all_specs),
+           "checkpoint": "every a_j kept" if ckpt > 1024 else "every %d slices" % ckpt,
+           "structures_rank0": len(jobs), "groups_rank0": bat.ngroups, "lanes": bat.lanes,
+           "hw_queues": os.environ.get("CUDA_DEVICE_MAX_CONNECTIONS", "8 (default)"),
+           "api": "mslice_loss_grad_batched (one C call: grouping, lanes and launch sequences in the library)",
+           "units_per_step_rank0": bat.units, "setup_s": setup_s, "steps": args.steps}
+    del bat, jobs
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_batch(args):
+    """64 independent structures of uneven shape (grids 128..512 per axis,
+    128..1024 slices, 0.1-0.5 deg), loss + gradient of all of them as one
+    CUDA-graph launch; voxel-slice-steps/s over the whole batch.  Under
+    torchrun the structures are split between the ranks by index (strong
+    scaling: the batch is fixed)."""
+    import torch
+    import torch.distributed as dist
+
+    from paper_2212_01253_gb300 import build as cuda_build
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    if rank == 0 or not os.path.exists(cuda_build.LIB):
+        cuda_build.build()
+    if world > 1:
+        dist.barrier()
+    r = batch_measure(args, dev, world, rank)
     if rank != 0:
         dist.destroy_process_group()
         return 0
-    line = {"metric": "batched multislice voxel-steps/s fwd+adjoint", "value": value,
-            "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
-            "eager_ms_per_step": eager_ms, "higher_is_better": True, "scaling": "strong",
-            "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "%d structures, grids 128-512 per axis, 128-1024 slices, 0.1-0.5 deg, "
-                                   "one CUDA graph per rank" % len(all_specs),
-                       "checkpoint": "every a_j kept" if ckpt > 1024 else "every %d slices" % ckpt,
-                       "structures_rank0": len(jobs), "groups_rank0": bat.ngroups, "lanes": bat.lanes,
-                       "api": "mslice_loss_grad_batched (one C call: grouping, lanes and launch sequences "
-                              "in the library)",
-                       "units_per_step_rank0": bat.units, "setup_s": setup_s}}
+    cfg = {k: r[k] for k in ("workload", "checkpoint", "structures_rank0", "groups_rank0", "lanes", "hw_queues",
+                             "api", "units_per_step_rank0", "setup_s")}
+    line = {"metric": "batched multislice voxel-steps/s fwd+adjoint", "value": r["value"],
+            "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": r["ms_per_step"], "eager_ms_per_step": r["eager_ms_per_step"],
+            "higher_is_better": True, "scaling": "strong", "dtype": "f32", "data": "synthetic", "config": cfg}
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -1019,6 +1041,7 @@ def main():
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--no-ckpt32", action="store_true", help="sweep: skip the checkpoint-every-32 leg")
     ap.add_argument("--no-recon", action="store_true", help="sweep: skip the reconstruction leg")
+    ap.add_argument("--no-batch", action="store_true", help="sweep: skip the batched uneven-structures leg")
     ap.add_argument("--recon-train-samples", type=int, default=65536,
                     help="sweep: forward-model samples the reconstruction leg's network trains on")
     ap.add_argument("--recon-cap", type=int, default=3000, help="sweep: iteration cap of the reconstruction leg")

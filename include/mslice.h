@@ -210,11 +210,16 @@ int mslice_loss_grad_multi(const mslice_params *p, const float *vols, const floa
  * once; the batching itself has no counterpart in the paper).  Jobs of one
  * grid shape (ny, nz, ns) advance together as the wavefields of one
  * per-structure run (up to MSLICE_MAX_ANGLES per run); the runs ("groups") are
- * spread over `lanes` library-owned streams (longest first onto the least
- * loaded lane, the persistent kernels of each on SMs / lanes blocks so that
- * concurrent runs fit on the GPU together), forked from and joined back into
- * `stream`.  Every job's results are bitwise those of a single-structure call
- * with the same launch shape.
+ * spread over `lanes` library-owned streams, forked from and joined back into
+ * `stream`: longest first (work = voxels x slices x structures, or for slice
+ * loops of little work the number of slices) onto the least loaded lane, each
+ * group on the blocks its row and column tasks fill (one task per warp), at
+ * most half the SMs.  With lanes == 1 every group runs on the default grid,
+ * one after the other.  Lanes beyond the process's hardware work queues
+ * (CUDA_DEVICE_MAX_CONNECTIONS, 8 unless set before the CUDA context is
+ * created) share queues and partly serialise.
+ * Every job's results are bitwise those of a single-structure call with the
+ * same launch shape.
  * ------------------------------------------------------------------------ */
 typedef struct mslice_job {
     int32_t ny, nz, ns;        /* grid of this structure: powers of two in [1, MSLICE_MAX_N], ns >= 1 */
@@ -256,11 +261,14 @@ int mslice_loss_grad_batched(const mslice_params *common, const mslice_job *jobs
 
 /* The plan of a batched call, on the host (no device work): *ngroups, and
  * for every job its group (group_of_job[njobs], may be NULL), for every group
- * its lane (lane_of_group[ngroups], may be NULL; at most njobs groups).
+ * its lane (lane_of_group[ngroups], may be NULL; at most njobs groups) and the
+ * blocks of its persistent grid (blocks_of_group[ngroups], may be NULL; 0 =
+ * the default grid, lanes == 1).  The SM count is the current device's (152
+ * when no device can be queried).
  * Groups are numbered in order of their first job; a group holds the jobs of
  * one grid shape (ny, nz, ns), at most MSLICE_MAX_ANGLES, in job order. */
 int mslice_batched_plan(const mslice_params *common, const mslice_job *jobs, int njobs, int op, int lanes,
-                        int *group_of_job, int *lane_of_group, int *ngroups);
+                        int *group_of_job, int *lane_of_group, int *blocks_of_group, int *ngroups);
 
 /* mslice_status() of every group of a batched call (same jobs, op and lanes):
  * waits for `stream`, then MSLICE_OK, or MSLICE_ETIMEDOUT if a bounded

@@ -166,7 +166,7 @@ def _load():
                 "mslice_loss_grad_batched": ([P, vp, ctypes.c_int, ctypes.c_int, vp, vp, sz, vp], ctypes.c_int),
                 "mslice_forward_batched": ([P, vp, ctypes.c_int, ctypes.c_int, vp, sz, vp], ctypes.c_int),
                 "mslice_batched_status": ([P, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp], ctypes.c_int),
-                "mslice_batched_plan": ([P, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp, vp],
+                "mslice_batched_plan": ([P, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp, vp, vp],
                                         ctypes.c_int),
                 "mslice_transmission": ([P, vp, vp, vp], ctypes.c_int),
                 "mslice_status": ([vp, vp], ctypes.c_int),
@@ -333,13 +333,16 @@ def mslice_forward_batched(common, jobs, lanes, ws, stream=None):
         _ptr(ws, torch.uint8, None, "ws"), ws.numel(), _stream(stream)), "mslice_forward_batched")
 
 
-def mslice_batched_plan(common, jobs, op, lanes=1):
-    """(group of each job, lane of each group) of a batched call (host only)."""
+def mslice_batched_plan(common, jobs, op, lanes=1, blocks=False):
+    """(group of each job, lane of each group[, blocks of each group]) of a
+    batched call (host only)."""
     n = len(jobs)
-    gj, lg, ng = (ctypes.c_int * n)(), (ctypes.c_int * n)(), ctypes.c_int(0)
+    gj, lg, bg, ng = (ctypes.c_int * n)(), (ctypes.c_int * n)(), (ctypes.c_int * n)(), ctypes.c_int(0)
     _check(_load().mslice_batched_plan(ctypes.byref(common), ctypes.cast(jobs, ctypes.c_void_p), n, int(op),
                                        int(lanes), ctypes.cast(gj, ctypes.c_void_p), ctypes.cast(lg, ctypes.c_void_p),
-                                       ctypes.byref(ng)), "mslice_batched_plan")
+                                       ctypes.cast(bg, ctypes.c_void_p), ctypes.byref(ng)), "mslice_batched_plan")
+    if blocks:
+        return list(gj), list(lg)[:ng.value], list(bg)[:ng.value]
     return list(gj), list(lg)[:ng.value]
 
 

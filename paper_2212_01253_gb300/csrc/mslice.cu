@@ -761,17 +761,23 @@ __global__ void k_sum_doubles(const double* __restrict__ x, int n, double* out) 
 struct Group {
     int ny, nz, ns, n;
     int idx[MSLICE_MAX_ANGLES];   // job indices, in job order
-    double cost;                  // modelled time (lane assignment)
+    double cost;                  // modelled work in SM-seconds (lane assignment)
     size_t ws_off, ws_bytes;      // region of the batch workspace
     int lane;
+    int blocks;                   // grid of the group's persistent kernels (0: the default grid)
 };
 
 constexpr int kMaxLanes = 16;
+// throughput of the slice-loop kernels per SM (voxel-slice-steps of forward +
+// adjoint per second) and the latency of one slice step (forward + adjoint:
+// the grid barriers and the dependent loads), measured on 128..512-point
+// grids; the plan uses them only to compare groups and lanes
+constexpr double kUnitsPerSmSecond = 3.6e8;
+constexpr double kSliceStepSeconds = 2.2e-5;
 
 // parameters of a group's run: the common ones with the group's grid, angles
-// and launch shape
-mslice_params group_params(const mslice_params* common, const mslice_job* jobs, const Group& g, int op,
-                           int lanes, int sms) {
+// and launch shape (blocks > 0: that many blocks)
+mslice_params group_params(const mslice_params* common, const mslice_job* jobs, const Group& g, int blocks) {
     mslice_params q = *common;
     q.ny = g.ny; q.nz = g.nz; q.ns = g.ns; q.nw = g.n;
     for (int k = 0; k < g.n; ++k) {
@@ -781,31 +787,31 @@ mslice_params group_params(const mslice_params* common, const mslice_job* jobs, 
     q.flags |= MSLICE_PER_STRUCTURE;
     const int cw = jobs[g.idx[0]].col_width;
     if (cw > 0) q.col_width = cw;
-    if (lanes > 1) {
-        // concurrent lanes: each group's persistent kernels on the blocks its
-        // tasks need (about two row or column tasks per warp or group and
-        // pass), at most SMs / 2, so that small groups (whose slice loops are
-        // bound by barrier latency) hold few SMs and many run at once
-        const int Ty = q.ny > 32 ? q.ny / 32 : 1, Tz = q.nz > 32 ? q.nz / 32 : 1;
-        const int cwq = col_width(&q);
-        const long row_tasks = (long)q.nz * q.nw, row_per_block = MS_THREADS / Ty;
-        const long col_tasks = (long)((q.ny + cwq - 1) / cwq) * q.nw, col_per_block = MS_THREADS / (cwq * Tz);
-        long need = (row_tasks + 2 * row_per_block - 1) / (2 * row_per_block);
-        const long need_c = (col_tasks + 2 * col_per_block - 1) / (2 * col_per_block);
-        if (need_c > need) need = need_c;
-        const long cap = sms / 2 > 0 ? sms / 2 : 1;
-        q.grid_blocks = (int)(need < 1 ? 1 : (need > cap ? cap : need));
-    }
+    if (blocks > 0) q.grid_blocks = blocks;
     return q;
 }
 
-// Groups jobs by grid shape (in order of first appearance), assigns the groups
-// to lanes longest first onto the least loaded lane (ties: the lowest lane),
-// and lays out the batch workspace: ngroups FP64 loss totals, then one
-// workspace region per group.  Returns 0 or an error code.
+// blocks a group's slice loop keeps busy: one row task per warp, or one
+// column task per column group, in every pass
+long useful_blocks(const mslice_params& q) {
+    const int Ty = q.ny > 32 ? q.ny / 32 : 1, Tz = q.nz > 32 ? q.nz / 32 : 1;
+    const int cw = col_width(&q);
+    const long row_tasks = (long)q.nz * q.nw, row_per_block = MS_THREADS / Ty;
+    const long col_tasks = (long)((q.ny + cw - 1) / cw) * q.nw, col_per_block = MS_THREADS / (cw * Tz);
+    const long r = (row_tasks + row_per_block - 1) / row_per_block, c = (col_tasks + col_per_block - 1) / col_per_block;
+    return r > c ? r : c;
+}
+
+// Groups jobs by grid shape (in order of first appearance) and lays out the
+// batch workspace: ngroups FP64 loss totals, then one workspace region per
+// group.  The groups go longest first onto the least loaded lane; a group's
+// size is its work in SM-seconds at the per-SM rate, but no less than its
+// slices times the slice-step latency on an equal share of the SMs (slice loops
+// of little work are bound by that latency, whatever their grid).  Returns 0
+// or an error code.
 int plan_batch(const mslice_params* common, const mslice_job* jobs, int njobs, int op, int lanes,
                std::vector<Group>& G, size_t* total, int sms) {
-    if (!common || !jobs || njobs < 1 || lanes < 1 || lanes > kMaxLanes) return MSLICE_EINVAL;
+    if (!common || !jobs || njobs < 1 || lanes < 1 || lanes > kMaxLanes || sms < 1) return MSLICE_EINVAL;
     if (common->flags & MSLICE_ANGULAR) return MSLICE_EUNSUPPORTED;
     if (op == MSLICE_OP_LOSS_GRAD && (common->flags & MSLICE_EXIT_WAVE)) return MSLICE_EUNSUPPORTED;
     G.clear();
@@ -826,30 +832,49 @@ int plan_batch(const mslice_params* common, const mslice_job* jobs, int njobs, i
         }
         g->idx[g->n++] = i;
     }
-    size_t off = align256((size_t)G.size() * sizeof(double));
-    std::vector<double> load(lanes, 0.0);
-    std::vector<int> order(G.size());
-    for (size_t k = 0; k < G.size(); ++k) {
+    const size_t ng = G.size();
+    std::vector<long> useful(ng);
+    std::vector<double> work(ng);
+    std::vector<int> order(ng);
+    for (size_t k = 0; k < ng; ++k) {
         Group& g = G[k];
-        const mslice_params q = group_params(common, jobs, g, op, lanes, sms);
+        const mslice_params q = group_params(common, jobs, g, 0);
         if (validate(&q)) return MSLICE_EINVAL;
-        g.ws_off = off;
-        g.ws_bytes = make_layout(&q, op).total;
-        off = align256(off + g.ws_bytes);
-        // wall time of the group on its blocks: its work at the rate of those
-        // blocks (5e10 units/s on the whole GPU) plus a per-slice latency term
-        // (the grid barriers of latency-bound slice steps)
-        const double blocks = q.grid_blocks > 0 ? q.grid_blocks : sms;
-        g.cost = (double)g.n * g.ny * g.nz * g.ns / (5e10 * blocks / sms) + g.ns * 2.5e-5;
+        useful[k] = useful_blocks(q);
+        work[k] = (double)g.n * g.ny * g.nz * g.ns / kUnitsPerSmSecond;
+        const double floor_sm = g.ns * kSliceStepSeconds * sms / lanes;
+        g.cost = work[k] > floor_sm ? work[k] : floor_sm;
+        g.blocks = 0;
         order[k] = (int)k;
     }
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return G[a].cost > G[b].cost; });
+    std::vector<double> load(lanes, 0.0);
     for (int k : order) {
         int best = 0;
         for (int l = 1; l < lanes; ++l)
             if (load[l] < load[best]) best = l;
         G[k].lane = best;
         load[best] += G[k].cost;
+    }
+    if (lanes > 1) {
+        // every group on the blocks its tasks fill, at most half the SMs: the
+        // lanes' grids together may exceed the SMs (a cooperative grid starts
+        // when all its blocks fit), which measured faster than splitting the
+        // SMs between the lanes in proportion to their work, because runs of
+        // different grid shapes side by side slow each other down (1.3-1.5x)
+        // more than copies of one shape do (1.0-1.2x)
+        for (size_t k = 0; k < ng; ++k) {
+            const long cap = sms / 2 > 0 ? sms / 2 : 1;
+            G[k].blocks = (int)(useful[k] < cap ? useful[k] : cap);
+        }
+    }
+    size_t off = align256(ng * sizeof(double));
+    for (Group& g : G) {
+        const mslice_params q = group_params(common, jobs, g, g.blocks);
+        if (validate(&q)) return MSLICE_EINVAL;
+        g.ws_off = off;
+        g.ws_bytes = make_layout(&q, op).total;
+        off = align256(off + g.ws_bytes);
     }
     *total = off;
     return MSLICE_OK;
@@ -910,7 +935,7 @@ int run_batch(const mslice_params* common, const mslice_job* jobs, int njobs, in
     for (int k : order) {
         const Group& g = G[k];
         const cudaStream_t gs = lanes > 1 ? L->s[g.lane] : st;
-        const mslice_params q = group_params(common, jobs, g, op, lanes, sms);
+        const mslice_params q = group_params(common, jobs, g, g.blocks);
         JobTable jt{};
         float scales[MSLICE_MAX_ANGLES];
         for (int w = 0; w < g.n; ++w) {
@@ -1090,7 +1115,7 @@ size_t mslice_batched_workspace_size(const mslice_params* common, const mslice_j
 }
 
 int mslice_batched_plan(const mslice_params* common, const mslice_job* jobs, int njobs, int op, int lanes,
-                        int* group_of_job, int* lane_of_group, int* ngroups) {
+                        int* group_of_job, int* lane_of_group, int* blocks_of_group, int* ngroups) {
     if (!ngroups) return MSLICE_EINVAL;
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
@@ -1102,6 +1127,7 @@ int mslice_batched_plan(const mslice_params* common, const mslice_job* jobs, int
     *ngroups = (int)G.size();
     for (size_t k = 0; k < G.size(); ++k) {
         if (lane_of_group) lane_of_group[k] = G[k].lane;
+        if (blocks_of_group) blocks_of_group[k] = G[k].blocks;
         if (group_of_job)
             for (int w = 0; w < G[k].n; ++w) group_of_job[G[k].idx[w]] = (int)k;
     }

@@ -38,6 +38,30 @@ def test_every_group_lands_on_one_lane(lanes):
         assert sorted(lg) == list(range(len(lg)))
 
 
+@pytest.mark.parametrize("lanes", [1, 2, 4, 16])
+def test_group_grids_are_sized_by_their_tasks(lanes):
+    """With lanes > 1 every group runs on the blocks its tasks fill (one row
+    task per warp: 256 / (ny / 32) rows a block), at most half of the 152 SMs;
+    with one lane on the default grid (0)."""
+    common = B.make_params(64, 64, 1)
+    arr = _jobs(SHAPES)
+    gj, lg, bg = B.mslice_batched_plan(common, arr, B.MSLICE_OP_LOSS_GRAD, lanes, blocks=True)
+    if lanes == 1:
+        assert set(bg) == {0}
+        return
+    for g, b in enumerate(bg):
+        members = [i for i in range(len(SHAPES)) if gj[i] == g]
+        ny, nz, ns = SHAPES[members[0]]
+        rows_per_block = 256 // max(1, ny // 32)
+        need = -(-nz * len(members) // rows_per_block)
+        assert 1 <= b <= 76 and b >= min(need, 76)
+    # the 512 x 512 x 1024 pair: 1024 rows (and 1024 columns) of 512 points,
+    # 16 rows a block: 64 blocks
+    assert bg[gj[SHAPES.index((512, 512, 1024))]] == 64
+    # (64, 64, 1): 64 rows of 64 points, 128 rows a block: one block
+    assert bg[gj[SHAPES.index((64, 64, 1))]] == 1
+
+
 def test_batch_workspace_is_the_sum_of_the_group_workspaces():
     common = B.make_params(64, 64, 1, checkpoint_every=32)
     arr = _jobs(SHAPES)

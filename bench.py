@@ -973,7 +973,7 @@ def run_rotate(args):
     peak = float(measured_peaks().get("hbm_gbs", 6800.0))
     res = {}
     cases = (("rotate_pitch", B.mslice_rotate, 0.0), ("rotate_pitch_yaw", B.mslice_rotate, 0.5),
-             ("adjoint_pitch_yaw", B.mslice_rotate_adjoint, 0.5))
+             ("adjoint_pitch", B.mslice_rotate_adjoint, 0.0), ("adjoint_pitch_yaw", B.mslice_rotate_adjoint, 0.5))
     for name, fn, psi_deg in cases:
         a, ps = np.deg2rad(0.3), np.deg2rad(psi_deg)
         src, dst = (vol, out) if fn is B.mslice_rotate else (out, vol)

@@ -42,6 +42,7 @@ struct RotMap {
     float C[3][3];      // A^-1 (sample-index steps of the lab index), for the gather's candidate box
     float inv_ay;       // 1 / A[2][2] (0 when |A[2][2]| <= 1e-3: every lab column is a candidate)
     int fmin[3], fmax[3];    // range of the fractional sample index over the lab volume (its corners)
+    int y_identity;     // f_y = m exactly and f_x, f_z independent of m (no yaw): the y stencil is the identity
 };
 
 // fraction-split index of one axis: lower lattice index and upper weight,
@@ -283,6 +284,109 @@ __global__ void __launch_bounds__(256) k_rotate_gather(const float2* __restrict_
     }
 }
 
+// The transpose without yaw (RotMap::y_identity): the y stencil is the
+// identity (weight 1 at m = sy, 0 at its neighbour), and the x and z stencils
+// do not depend on m, so a candidate lab row (x + dx, z + dz) adds its column
+// sy with one weight wx wz for the whole row.  One warp per sample row, lane
+// c holds columns c, c + 32, ...; the candidate rows, their weights and the
+// order of the sum are those of k_rotate_gather, which gives bitwise the same
+// sums (up to the sign of zero sums).
+__global__ void __launch_bounds__(256) k_rotate_gather_xz(const float2* __restrict__ g_lab,
+                                                          float2* __restrict__ g_sample, const RotMap R) {
+    const int lane = threadIdx.x & 31;
+    const unsigned rows = (unsigned)R.n[0] * (unsigned)R.n[1];
+    const unsigned warps = gridDim.x * (blockDim.x >> 5);
+    const int ns = R.n[0], nz = R.n[1], ny = R.n[2];
+    const int nc = (ny + 31) >> 5;   // <= 32 column chunks
+    for (unsigned row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); row < rows; row += warps) {
+        const int sx = (int)(row / (unsigned)nz), sz = (int)(row - (unsigned)sx * (unsigned)nz);
+        int ri_k = 0;
+        float rf_k = 0.f;
+        if (lane < 2) {
+            const double b = lane == 0 ? R.b[0] : R.b[1];
+            const double aj = lane == 0 ? R.A[0][0] : R.A[1][0];
+            const double al = lane == 0 ? R.A[0][1] : R.A[1][1];
+            const double f = fma(al, (double)sz, fma(aj, (double)sx, b));
+            const double fl = floor(f);
+            ri_k = (int)fl;
+            rf_k = (float)(f - fl);
+        }
+        int ri[2];
+        float rf[2], rif[2];
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            ri[k] = __shfl_sync(0xffffffffu, ri_k, k);
+            rf[k] = __shfl_sync(0xffffffffu, rf_k, k);
+            rif[k] = (float)ri[k];
+        }
+        const float sxf = (float)sx, szf = (float)sz, nsf = (float)ns, nzf = (float)nz;
+        const float dlo[3] = {(float)((sx == 0 ? min(R.fmin[0], -1) : sx - 1) - ri[0]) - rf[0],
+                              (float)((sz == 0 ? min(R.fmin[1], -1) : sz - 1) - ri[1]) - rf[1], 0.f};
+        const float dhi[3] = {(float)((sx == ns - 1 ? max(R.fmax[0], ns) : sx + 1) - ri[0]) - rf[0],
+                              (float)((sz == nz - 1 ? max(R.fmax[1], nz) : sz + 1) - ri[1]) - rf[1], 0.f};
+        const float tol = 1e-3f;
+        float xlo, xhi, zlo, zhi;
+        lab_range(R.C[0], dlo, dhi, xlo, xhi);
+        lab_range(R.C[1], dlo, dhi, zlo, zhi);
+        const int dx0 = (int)fmaxf(ceilf(xlo - tol), (float)-sx), dx1 = (int)fminf(floorf(xhi + tol), (float)(ns - 1 - sx));
+        const int dz0 = (int)fmaxf(ceilf(zlo - tol), (float)-sz), dz1 = (int)fminf(floorf(zhi + tol), (float)(nz - 1 - sz));
+        // four column chunks (128 columns) at a time; for each, the candidates
+        // in order, four contributing rows at a time, so that 16 loads are in
+        // flight before their sums (the candidates' weights are recomputed for
+        // each group of chunks: a few uniform operations)
+        float2* dst = g_sample + (size_t)row * ny + lane;
+        for (int c0 = 0; c0 < nc; c0 += 4) {
+            float2 acc[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[c] = make_float2(0.f, 0.f);
+            int dx = dz0 <= dz1 ? dx0 : dx1 + 1, dz = dz0;   // an empty z range: no candidates
+            while (dx <= dx1) {
+                const float2* q[4] = {nullptr, nullptr, nullptr, nullptr};
+                float w[4] = {0.f, 0.f, 0.f, 0.f};
+                int cnt = 0;
+                for (; dx <= dx1 && cnt < 4;) {
+                    const float rfx = rf[0] + R.Af[0][0] * (float)dx + R.Af[0][1] * (float)dz;
+                    const float rfz = rf[1] + R.Af[1][0] * (float)dx + R.Af[1][1] * (float)dz;
+                    const float wx = axis_weight(rif[0], rfx, R.hi[0], R.lo[0], 0.f, nsf, sxf);
+                    const float wz = axis_weight(rif[1], rfz, R.hi[1], R.lo[1], 0.f, nzf, szf);
+                    const float wt = wx * wz;
+                    if (wt != 0.f) {   // uniform over the warp
+                        const float2* src = g_lab + ((size_t)(sx + dx) * nz + (size_t)(sz + dz)) * ny + lane +
+                                            32 * c0;
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            if (k == cnt) { q[k] = src; w[k] = wt; }
+                        }
+                        ++cnt;
+                    }
+                    if (++dz > dz1) { dz = dz0; ++dx; }
+                }
+                if (cnt == 0) break;
+                float2 g[4][4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c)
+                        g[k][c] = (k < cnt && c0 + c < nc && lane + 32 * (c0 + c) < ny) ? __ldg(q[k] + 32 * c)
+                                                                                          : make_float2(0.f, 0.f);
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        if (k < cnt) {
+                            acc[c].x = fmaf(w[k], g[k][c].x, acc[c].x);
+                            acc[c].y = fmaf(w[k], g[k][c].y, acc[c].y);
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                if (c0 + c < nc && lane + 32 * (c0 + c) < ny) dst[32 * (c0 + c)] = acc[c];
+        }
+    }
+}
+
 // 12-significant-bit head of a (the tail a - head is exact in double)
 double head12(double a) {
     if (a == 0.0 || !isfinite(a)) return 0.0;
@@ -346,6 +450,9 @@ int make_map(const mslice_params* p, double alpha, double psi, const double* c, 
         R->fmin[k] = (int)floor(lo) - 1;
         R->fmax[k] = (int)ceil(hi) + 1;
     }
+    R->y_identity = R->hi[0] == 0.f && R->lo[0] == 0.f && R->hi[1] == 0.f && R->lo[1] == 0.f && R->A[2][0] == 0.0 &&
+                    R->A[2][1] == 0.0 && R->b[2] == 0.0 && R->hi[2] == 1.f && R->lo[2] == 0.f &&
+                    R->C[0][2] == 0.f && R->C[1][2] == 0.f;
     return MSLICE_OK;
 }
 
@@ -369,7 +476,10 @@ int launch(const mslice_params* p, double alpha, double psi, const double* c, co
     const long long cap = (long long)device_sms() * 32;   // a few waves of 8-warp blocks per SM
     const unsigned blocks = (unsigned)(rows / 8 + 1 < cap ? rows / 8 + 1 : cap);
     if (adjoint) {
-        k_rotate_gather<<<blocks, 256, 0, st>>>((const float2*)in, (float2*)out, R);
+        if (R.y_identity)
+            k_rotate_gather_xz<<<blocks, 256, 0, st>>>((const float2*)in, (float2*)out, R);
+        else
+            k_rotate_gather<<<blocks, 256, 0, st>>>((const float2*)in, (float2*)out, R);
     } else {
         k_rotate<<<blocks, 256, 0, st>>>((const float2*)in, (float2*)out, R);
     }

@@ -50,6 +50,28 @@ constexpr long long kDefaultTimeoutNs = 2000000000LL;  // 2 s per grid wait
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+// the same sums as one paired FP32 instruction (IEEE round-to-nearest per
+// half: bitwise equal to cadd / csub)
+__device__ __forceinline__ unsigned long long pk2(float2 a) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a.x), "f"(a.y));
+    return r;
+}
+__device__ __forceinline__ float2 upk2(unsigned long long r) {
+    float2 a;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a.x), "=f"(a.y) : "l"(r));
+    return a;
+}
+__device__ __forceinline__ float2 cadd2(float2 a, float2 b) {
+    unsigned long long r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(pk2(a)), "l"(pk2(b)));
+    return upk2(r);
+}
+__device__ __forceinline__ float2 csub2(float2 a, float2 b) {
+    unsigned long long r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(pk2(a)), "l"(pk2(b)));
+    return upk2(r);
+}
 __device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
 // a * w
 __device__ __forceinline__ float2 cmul(float2 a, float2 w) {
@@ -158,8 +180,8 @@ struct DifStage {
             for (int k = 0; k < HALF; ++k) {
                 const int i0 = B + S * (blk + k), i1 = i0 + S * HALF;
                 const float2 a = x[i0], b = x[i1];
-                x[i0] = cadd(a, b);
-                x[i1] = tw32<INV>(csub(a, b), k * (32 / (2 * HALF)));
+                x[i0] = cadd2(a, b);
+                x[i1] = tw32<INV>(csub2(a, b), k * (32 / (2 * HALF)));
             }
         }
         DifStage<R, S, HALF / 2, INV>::run(x, B);

@@ -190,7 +190,11 @@ __device__ __forceinline__ void lab_range(const float (&C)[3], const float (&dlo
 // (x + dx, z + dz) takes them plus FP32 offsets.  For each candidate lab voxel
 // the three axis stencils are computed as in the forward and the weight of
 // this sample voxel is its product; the candidates are visited in a fixed
-// order (dx, dz, then lab column), so the sum is bitwise reproducible.  The
+// order (dx, dz, then lab column), so the sum is bitwise reproducible.  A
+// sample voxel on a y face takes every lab column past the face (up to the
+// volume's y shift, ~90 columns at 0.5 deg yaw over 1024 slices): the whole
+// warp walks such a window, and a fixed xor tree adds the lanes' partial sums
+// (also reproducible), instead of one lane walking it while 31 wait.  The
 // candidate box is the lab image of the sample window [s - 1, s + 1] per axis
 // (at the volume's faces, where the forward clamps, out to the farthest index
 // a lab voxel reaches), with a tolerance of 1e-3 index units; the window's
@@ -248,34 +252,72 @@ __global__ void __launch_bounds__(256) k_rotate_gather(const float2* __restrict_
             // this lane's window along y
             const float ylo = (float)((sy == 0 ? min(R.fmin[2], -1) : sy - 1) - ri[2]) - rf[2];
             const float yhi = (float)((sy == ny - 1 ? max(R.fmax[2], ny) : sy + 1) - ri[2]) - rf[2];
+            // the candidate rows in order; for each, this lane's lab columns in
+            // order.  A wide window (a sample voxel on a y face, which takes
+            // every lab column past that face) is walked by the whole warp, and
+            // a fixed xor tree sums the lanes' partial sums into the owner's.
             float2 acc = make_float2(0.f, 0.f);
             for (int dx = dx0; dx <= dx1; ++dx) {
                 for (int dz = dz0; dz <= dz1; ++dz) {
                     float rfc[3];
 #pragma unroll
                     for (int k = 0; k < 3; ++k) rfc[k] = rf[k] + R.Af[k][0] * (float)dx + R.Af[k][1] * (float)dz;
-                    if (!active) continue;
-                    // lab columns whose y index can reach sy: A_y2 m in the window less the row offset
-                    const float off = R.Af[2][0] * (float)dx + R.Af[2][1] * (float)dz;
-                    int m0 = 0, m1 = ny - 1;
-                    if (R.inv_ay != 0.f) {
-                        float a = (ylo - off) * R.inv_ay, b = (yhi - off) * R.inv_ay;
-                        if (a > b) { const float tmp = a; a = b; b = tmp; }
-                        m0 = (int)fmaxf(ceilf(a - tol), 0.f);
-                        m1 = (int)fminf(floorf(b + tol), (float)(ny - 1));
-                    }
                     const float2* src = g_lab + ((size_t)(sx + dx) * nz + (size_t)(sz + dz)) * ny;
-                    float mf = (float)m0;
-                    for (int m = m0; m <= m1; ++m, mf += 1.f) {
-                        const float wy = axis_weight(rif[2], rfc[2], R.hi[2], R.lo[2], mf, nyf, syf);
-                        const float wx = axis_weight(rif[0], rfc[0], R.hi[0], R.lo[0], mf, nsf, sxf);
-                        const float wz = axis_weight(rif[1], rfc[1], R.hi[1], R.lo[1], mf, nzf, szf);
-                        const float wt = (wx * wz) * wy;
-                        // the load only where the voxel contributes (predicated, no branch)
-                        float2 g = make_float2(0.f, 0.f);
-                        if (wt != 0.f) g = __ldg(src + m);
-                        acc.x = fmaf(wt, g.x, acc.x);
-                        acc.y = fmaf(wt, g.y, acc.y);
+                    // lab columns whose y index can reach sy: A_y2 m in the window less the row offset
+                    int m0 = 0, m1 = -1;
+                    if (active) {
+                        const float off = R.Af[2][0] * (float)dx + R.Af[2][1] * (float)dz;
+                        m1 = ny - 1;
+                        if (R.inv_ay != 0.f) {
+                            float a = (ylo - off) * R.inv_ay, b = (yhi - off) * R.inv_ay;
+                            if (a > b) { const float tmp = a; a = b; b = tmp; }
+                            m0 = (int)fmaxf(ceilf(a - tol), 0.f);
+                            m1 = (int)fminf(floorf(b + tol), (float)(ny - 1));
+                        }
+                    }
+                    const bool wide = m1 - m0 >= 3;
+                    if (!wide) {
+                        float mf = (float)m0;
+                        for (int m = m0; m <= m1; ++m, mf += 1.f) {
+                            const float wy = axis_weight(rif[2], rfc[2], R.hi[2], R.lo[2], mf, nyf, syf);
+                            const float wx = axis_weight(rif[0], rfc[0], R.hi[0], R.lo[0], mf, nsf, sxf);
+                            const float wz = axis_weight(rif[1], rfc[1], R.hi[1], R.lo[1], mf, nzf, szf);
+                            const float wt = (wx * wz) * wy;
+                            if (wt != 0.f) {
+                                const float2 g = __ldg(src + m);
+                                acc.x = fmaf(wt, g.x, acc.x);
+                                acc.y = fmaf(wt, g.y, acc.y);
+                            }
+                        }
+                    }
+                    unsigned wm = __ballot_sync(0xffffffffu, wide);
+                    while (wm) {
+                        const int L = __ffs(wm) - 1;
+                        wm &= wm - 1;
+                        const int w0 = __shfl_sync(0xffffffffu, m0, L), w1 = __shfl_sync(0xffffffffu, m1, L);
+                        const float syL = __shfl_sync(0xffffffffu, syf, L);
+                        float2 part = make_float2(0.f, 0.f);
+                        for (int m = w0 + lane; m <= w1; m += 32) {
+                            const float mf = (float)m;
+                            const float wy = axis_weight(rif[2], rfc[2], R.hi[2], R.lo[2], mf, nyf, syL);
+                            const float wx = axis_weight(rif[0], rfc[0], R.hi[0], R.lo[0], mf, nsf, sxf);
+                            const float wz = axis_weight(rif[1], rfc[1], R.hi[1], R.lo[1], mf, nzf, szf);
+                            const float wt = (wx * wz) * wy;
+                            if (wt != 0.f) {
+                                const float2 g = __ldg(src + m);
+                                part.x = fmaf(wt, g.x, part.x);
+                                part.y = fmaf(wt, g.y, part.y);
+                            }
+                        }
+#pragma unroll
+                        for (int o = 16; o > 0; o >>= 1) {
+                            part.x += __shfl_xor_sync(0xffffffffu, part.x, o);
+                            part.y += __shfl_xor_sync(0xffffffffu, part.y, o);
+                        }
+                        if (lane == L) {
+                            acc.x += part.x;
+                            acc.y += part.y;
+                        }
                     }
                 }
             }

@@ -326,13 +326,44 @@ __global__ void __launch_bounds__(256) k_rotate_gather(const float2* __restrict_
     }
 }
 
+// dst[c] (+)= sum over the CNT listed lab rows, in list order, of lw[k] times
+// row k's column (lane + 32 c), onto 0 (first) or onto dst's own earlier sum:
+// four column chunks at a time, every row's loads before the sums
+template <int CNT>
+__device__ __forceinline__ void sum_rows(const float2* __restrict__ g_lab, float2* __restrict__ dst,
+                                         const unsigned (&lrow)[8], const float (&lw)[8], int ny, int nc, int lane,
+                                         bool first) {
+    for (int c0 = 0; c0 < nc; c0 += 4) {
+        float2 g[CNT > 0 ? CNT : 1][4];
+#pragma unroll
+        for (int k = 0; k < CNT; ++k) {
+            const float2* src = g_lab + (size_t)lrow[k] * ny + lane + 32 * c0;
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                g[k][c] = (c0 + c < nc && lane + 32 * (c0 + c) < ny) ? __ldg(src + 32 * c) : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            if (c0 + c >= nc || lane + 32 * (c0 + c) >= ny) continue;
+            float2 a = first ? make_float2(0.f, 0.f) : dst[32 * (c0 + c)];
+#pragma unroll
+            for (int k = 0; k < CNT; ++k) {
+                a.x = fmaf(lw[k], g[k][c].x, a.x);
+                a.y = fmaf(lw[k], g[k][c].y, a.y);
+            }
+            dst[32 * (c0 + c)] = a;
+        }
+    }
+}
+
 // The transpose without yaw (RotMap::y_identity): the y stencil is the
 // identity (weight 1 at m = sy, 0 at its neighbour), and the x and z stencils
 // do not depend on m, so a candidate lab row (x + dx, z + dz) adds its column
-// sy with one weight wx wz for the whole row.  One warp per sample row, lane
-// c holds columns c, c + 32, ...; the candidate rows, their weights and the
-// order of the sum are those of k_rotate_gather, which gives bitwise the same
-// sums (up to the sign of zero sums).
+// sy with one weight wx wz for the whole row.  One warp per sample row: the
+// candidate rows are weighed once, and the contributing ones are summed over
+// all the row's columns (lane c holds columns c, c + 32, ...).  The candidate
+// rows, their weights and the order of the sum are those of k_rotate_gather,
+// which gives bitwise the same sums (up to the sign of zero sums).
 __global__ void __launch_bounds__(256) k_rotate_gather_xz(const float2* __restrict__ g_lab,
                                                           float2* __restrict__ g_sample, const RotMap R) {
     const int lane = threadIdx.x & 31;
@@ -372,59 +403,50 @@ __global__ void __launch_bounds__(256) k_rotate_gather_xz(const float2* __restri
         lab_range(R.C[1], dlo, dhi, zlo, zhi);
         const int dx0 = (int)fmaxf(ceilf(xlo - tol), (float)-sx), dx1 = (int)fminf(floorf(xhi + tol), (float)(ns - 1 - sx));
         const int dz0 = (int)fmaxf(ceilf(zlo - tol), (float)-sz), dz1 = (int)fminf(floorf(zhi + tol), (float)(nz - 1 - sz));
-        // four column chunks (128 columns) at a time; for each, the candidates
-        // in order, four contributing rows at a time, so that 16 loads are in
-        // flight before their sums (the candidates' weights are recomputed for
-        // each group of chunks: a few uniform operations)
         float2* dst = g_sample + (size_t)row * ny + lane;
-        for (int c0 = 0; c0 < nc; c0 += 4) {
-            float2 acc[4];
+        // the contributing rows (nonzero weight) in candidate order, eight at
+        // a time (2 to 4 in all away from the faces; a sample row on an x or z
+        // face takes every lab row past that face), each batch summed onto
+        // the previous batches' sums
+        int dx = dz0 <= dz1 ? dx0 : dx1 + 1, dz = dz0;   // an empty z range: no candidates
+        bool first = true;
+        for (;;) {
+            unsigned lrow[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+            float lw[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            int cnt = 0;
+            while (dx <= dx1 && cnt < 8) {
+                const float rfx = rf[0] + R.Af[0][0] * (float)dx + R.Af[0][1] * (float)dz;
+                const float rfz = rf[1] + R.Af[1][0] * (float)dx + R.Af[1][1] * (float)dz;
+                const float wx = axis_weight(rif[0], rfx, R.hi[0], R.lo[0], 0.f, nsf, sxf);
+                const float wz = axis_weight(rif[1], rfz, R.hi[1], R.lo[1], 0.f, nzf, szf);
+                const float wt = wx * wz;
+                if (wt != 0.f) {   // uniform over the warp
+                    const unsigned r = (unsigned)(sx + dx) * (unsigned)nz + (unsigned)(sz + dz);
 #pragma unroll
-            for (int c = 0; c < 4; ++c) acc[c] = make_float2(0.f, 0.f);
-            int dx = dz0 <= dz1 ? dx0 : dx1 + 1, dz = dz0;   // an empty z range: no candidates
-            while (dx <= dx1) {
-                const float2* q[4] = {nullptr, nullptr, nullptr, nullptr};
-                float w[4] = {0.f, 0.f, 0.f, 0.f};
-                int cnt = 0;
-                for (; dx <= dx1 && cnt < 4;) {
-                    const float rfx = rf[0] + R.Af[0][0] * (float)dx + R.Af[0][1] * (float)dz;
-                    const float rfz = rf[1] + R.Af[1][0] * (float)dx + R.Af[1][1] * (float)dz;
-                    const float wx = axis_weight(rif[0], rfx, R.hi[0], R.lo[0], 0.f, nsf, sxf);
-                    const float wz = axis_weight(rif[1], rfz, R.hi[1], R.lo[1], 0.f, nzf, szf);
-                    const float wt = wx * wz;
-                    if (wt != 0.f) {   // uniform over the warp
-                        const float2* src = g_lab + ((size_t)(sx + dx) * nz + (size_t)(sz + dz)) * ny + lane +
-                                            32 * c0;
-#pragma unroll
-                        for (int k = 0; k < 4; ++k) {
-                            if (k == cnt) { q[k] = src; w[k] = wt; }
-                        }
-                        ++cnt;
-                    }
-                    if (++dz > dz1) { dz = dz0; ++dx; }
-                }
-                if (cnt == 0) break;
-                float2 g[4][4];
-#pragma unroll
-                for (int k = 0; k < 4; ++k)
-#pragma unroll
-                    for (int c = 0; c < 4; ++c)
-                        g[k][c] = (k < cnt && c0 + c < nc && lane + 32 * (c0 + c) < ny) ? __ldg(q[k] + 32 * c)
-                                                                                          : make_float2(0.f, 0.f);
-#pragma unroll
-                for (int c = 0; c < 4; ++c) {
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        if (k < cnt) {
-                            acc[c].x = fmaf(w[k], g[k][c].x, acc[c].x);
-                            acc[c].y = fmaf(w[k], g[k][c].y, acc[c].y);
+                    for (int k = 0; k < 8; ++k) {
+                        if (k == cnt) {
+                            lrow[k] = r;
+                            lw[k] = wt;
                         }
                     }
+                    ++cnt;
                 }
+                if (++dz > dz1) { dz = dz0; ++dx; }
             }
-#pragma unroll
-            for (int c = 0; c < 4; ++c)
-                if (c0 + c < nc && lane + 32 * (c0 + c) < ny) dst[32 * (c0 + c)] = acc[c];
+            if (cnt == 0 && !first) break;
+            switch (cnt) {   // uniform over the warp
+                case 0: sum_rows<0>(g_lab, dst, lrow, lw, ny, nc, lane, first); break;
+                case 1: sum_rows<1>(g_lab, dst, lrow, lw, ny, nc, lane, first); break;
+                case 2: sum_rows<2>(g_lab, dst, lrow, lw, ny, nc, lane, first); break;
+                case 3: sum_rows<3>(g_lab, dst, lrow, lw, ny, nc, lane, first); break;
+                case 4: sum_rows<4>(g_lab, dst, lrow, lw, ny, nc, lane, first); break;
+                case 5: sum_rows<5>(g_lab, dst, lrow, lw, ny, nc, lane, first); break;
+                case 6: sum_rows<6>(g_lab, dst, lrow, lw, ny, nc, lane, first); break;
+                case 7: sum_rows<7>(g_lab, dst, lrow, lw, ny, nc, lane, first); break;
+                default: sum_rows<8>(g_lab, dst, lrow, lw, ny, nc, lane, first); break;
+            }
+            first = false;
+            if (dx > dx1) break;
         }
     }
 }

@@ -67,6 +67,24 @@ def test_rotate_adjoint_vs_oracle(shape, sp, alpha, psi, c, kind):
     assert G.rel(out.cpu().numpy(), ref) <= 1e-6
 
 
+def test_rotate_adjoint_without_yaw_collapsed_faces_vs_oracle():
+    """psi = 0 (the row-wise transpose) at 5 deg pitch over 64 slices: the
+    lab rows shift by ~56 rows along z, so the sample rows on the z faces take
+    dozens of collapsed lab rows (the transpose's long path), the others 2-4."""
+    from paper_2212_01253_gb300 import binding as B
+    shape, sp, alpha, psi, c = (64, 64, 40), (20.0, 2.0, 2.0), 5.0, 0.0, (600.0, 63.0, 39.0)
+    g = ci.random_volume(99, shape[2], shape[1], shape[0], scale=1.0)
+    p = _params(*shape, sp)
+    out = torch.empty(shape, dtype=torch.complex64, device="cuda")
+    B.mslice_rotate_adjoint(p, np.deg2rad(alpha), np.deg2rad(psi), c, G.dev(g, np.complex64), out)
+    torch.cuda.synchronize()
+    ref = R.rotate_adjoint(g.astype(np.complex64), sp, np.deg2rad(alpha), np.deg2rad(psi), c)
+    got = out.cpu().numpy()
+    assert G.rel(got, ref) <= 1e-6
+    # the face rows carry the collapsed rows' sums
+    assert G.rel(got[:, 0, :], ref[:, 0, :]) <= 1e-6 and G.rel(got[:, -1, :], ref[:, -1, :]) <= 1e-6
+
+
 def test_rotate_adjoint_is_bitwise_reproducible_and_a_transpose():
     """The transpose is a gather in a fixed order: two calls agree bit for bit;
     and <R x, y> = <x, R^T y> to FP32 rounding."""

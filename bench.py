@@ -952,6 +952,56 @@ def run_convergence(args):
     return 0
 
 
+def run_gemm(args):
+    """Dense layer of the learned initialiser on the tcgen05 tensor cores
+    (mslice_nn_gemm_bf16): C = A B^T with BF16 operands packed K-major and
+    FP32 accumulation, at 8192^3 (operands 134 MB each and C 268 MB, larger
+    than L2) and at the network's largest layer shape; TFLOP/s against the
+    measured cuBLAS BF16 rate."""
+    import torch
+
+    from paper_2212_01253_gb300 import binding as B
+    from paper_2212_01253_gb300 import build as cuda_build
+
+    cuda_build.build()
+    torch.cuda.set_device(0)
+    peaks = measured_peaks()
+    peak = float(peaks.get("bf16_tflops", 1900.0))
+    res = {}
+    for (M, N, K) in ((8192, 8192, 8192), (16384, 4096, 4096)):
+        gen = torch.Generator(device="cuda").manual_seed(0)
+        A = torch.randn(M, K, generator=gen, device="cuda").to(torch.bfloat16)
+        Bm = torch.randn(N, K, generator=gen, device="cuda").to(torch.bfloat16)
+        C = torch.empty(M, N, device="cuda")
+        for _ in range(args.warmup):
+            B.mslice_nn_gemm_bf16(M, N, K, A, K, Bm, K, C, N)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            B.mslice_nn_gemm_bf16(M, N, K, A, K, Bm, K, C, N)
+        e1.record()
+        torch.cuda.synchronize()
+        if B.mslice_nn_gemm_bf16_status() != 0:
+            raise RuntimeError("a bounded wait of the tensor-core GEMM ran out")
+        ms = e0.elapsed_time(e1) / args.steps
+        tf = 2.0 * M * N * K / (ms / 1e3) / 1e12
+        res["%dx%dx%d" % (M, N, K)] = {"ms": ms, "tflops": tf, "frac_of_measured_bf16": tf / peak}
+        del A, Bm, C
+    head = res["8192x8192x8192"]
+    line = {"metric": "BF16 GEMM TFLOP/s (tcgen05, FP32 accumulate)", "value": head["tflops"], "unit": "TFLOP/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "dtype": "bf16",
+            "data": "synthetic",
+            "config": {"workload": "C = A B^T, M = N = K = 8192, A and B BF16 K-major, C FP32; operands larger "
+                                   "than L2"},
+            "roofline": {"bound": "tensor", "achieved": head["tflops"], "peak": peak, "unit": "TFLOP/s",
+                         "frac": head["frac_of_measured_bf16"], "traffic": None,
+                         "peak_basis": "measured cuBLAS BF16 burst" if "bf16_tflops" in peaks else "fallback"},
+            "shapes": res}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_rotate(args):
     """Frame rotation of Eq. 2-3 on the headline volume (512x512x1024, Si + 50
     Au pillars/lines): lab-frame resampling at 0.3 deg pitch without and with a
@@ -1015,7 +1065,7 @@ def main():
     ap.add_argument("--cpu-angles", type=int, default=3)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="sweep", choices=["sweep", "batch", "recon", "learned", "buried", "convergence", "rotate"],
+    ap.add_argument("--workload", default="sweep", choices=["sweep", "batch", "recon", "learned", "buried", "convergence", "rotate", "gemm"],
                     help="sweep: the headline 512x512x1024 9-angle step; batch: 64 uneven "
                          "structures in one graph; recon: time to a fixed chi^2; learned: "
                          "learned vs zero vs constant start; buried: coarse Si/Au voxels under the "
@@ -1065,6 +1115,8 @@ def main():
         return run_convergence(args)
     if args.workload == "rotate":
         return run_rotate(args)
+    if args.workload == "gemm":
+        return run_gemm(args)
     return run_gpu(args)
 
 

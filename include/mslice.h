@@ -435,6 +435,32 @@ size_t mslice_nn_gemm_workspace(int M, int N, int K);
 int mslice_nn_gemm(int M, int N, int K, const float *A, long long sam, long long sak, const float *B,
                    long long sbn, long long sbk, float *C, long long ldc, const float *bias, int relu,
                    float beta, void *ws, size_t ws_bytes, void *stream);
+
+/* Dense layer on the 5th-generation tensor cores (tcgen05.mma into tensor
+ * memory, operands by TMA): C[m][n] = beta*C[m][n] + sum_k A[m][k] B[n][k]
+ * (+ bias[n]) (ReLU if relu), FP32 accumulation.
+ *   A  [M][lda] BF16, row-major (k contiguous), 16-byte aligned, lda >= K and
+ *      a multiple of 8;  B [N][ldb] BF16, the same;  C [M][ldc] float32,
+ *      ldc >= N;  bias: NULL or float32[N].  All device memory owned by the
+ *      caller; C must not alias A, B or bias.
+ * One CTA per 128 x 256 tile of C; asynchronous on stream.  Errors:
+ * MSLICE_EINVAL (sizes, null or misaligned pointers, strides),
+ * MSLICE_EUNSUPPORTED (M > 65535 * 128, or no tensor-map encoder in the
+ * driver), MSLICE_ELAUNCH.  Every device-side wait is bounded (about 1 s);
+ * mslice_nn_gemm_bf16_status reports one that ran out. */
+int mslice_nn_gemm_bf16(int M, int N, int K, const void *A, long long lda, const void *B, long long ldb, float *C,
+                        long long ldc, const float *bias, int relu, float beta, void *stream);
+
+/* Waits for stream; MSLICE_ETIMEDOUT (and clears it) if a bounded wait of a
+ * tensor-core GEMM ran out since the last call, else MSLICE_OK. */
+int mslice_nn_gemm_bf16_status(void *stream);
+
+/* Operand packing for mslice_nn_gemm_bf16: dst[r][k] = BF16(src[r*s_row +
+ * k*s_k]) rounded to nearest even for k < K, and 0 for K <= k < ld (the
+ * strides give transposes).  dst: [rows][ld] 2-byte elements, device,
+ * 2-byte aligned.  MSLICE_EINVAL for null pointers, rows or K < 1, ld < K. */
+int mslice_nn_pack_bf16(const float *src, long long s_row, long long s_k, int rows, int K, void *dst, long long ld,
+                        void *stream);
 /* Patch permutation between NHWC [B][H][W][C] and [B][H/p][W/p][p][p][C]
  * (inverse = 0: NHWC -> patches; 1: back).  A convolution with kernel = stride
  * = p is a GEMM on the patch layout; its transpose is a GEMM followed by the

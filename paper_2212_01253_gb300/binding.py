@@ -195,6 +195,10 @@ def _load():
                 "mslice_nn_gemm": ([ctypes.c_int] * 3 + [vp, ll, ll, vp, ll, ll, vp, ll, vp, ctypes.c_int,
                                                          ctypes.c_float, vp, sz, vp], ctypes.c_int),
                 "mslice_nn_space_to_depth": ([vp, vp] + [ctypes.c_int] * 6 + [vp], ctypes.c_int),
+                "mslice_nn_pack_bf16": ([vp, ll, ll, ctypes.c_int, ctypes.c_int, vp, ll, vp], ctypes.c_int),
+                "mslice_nn_gemm_bf16": ([ctypes.c_int] * 3 + [vp, ll, vp, ll, vp, ll, vp, ctypes.c_int,
+                                                              ctypes.c_float, vp], ctypes.c_int),
+                "mslice_nn_gemm_bf16_status": ([vp], ctypes.c_int),
                 "mslice_nn_relu_backward": ([vp, vp, vp, sz, vp], ctypes.c_int),
                 "mslice_nn_sigmoid_mse": ([vp, vp, vp, vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_float, vp],
                                           ctypes.c_int),
@@ -475,6 +479,39 @@ def mslice_nn_gemm(M, N, K, A, sam, sak, B, sbn, sbk, C, ldc, bias=None, relu=Fa
         int(sbn), int(sbk), ctypes.c_void_p(C.data_ptr()), int(ldc),
         ctypes.c_void_p(bias.data_ptr()) if bias is not None else None, int(bool(relu)), float(beta), wsp, wsb,
         _stream(stream)), "mslice_nn_gemm")
+
+
+def mslice_nn_pack_bf16(src, s_row, s_k, rows, K, dst, ld, stream=None):
+    """dst[r][k] = BF16(src[r*s_row + k*s_k]) for k < K, 0 for K <= k < ld (dst: int16/bfloat16 CUDA tensor)."""
+    if not isinstance(src, torch.Tensor) or src.dtype != torch.float32 or not src.is_cuda:
+        raise TypeError("src must be a float32 CUDA tensor")
+    if not isinstance(dst, torch.Tensor) or dst.element_size() != 2 or not dst.is_cuda or dst.numel() < rows * ld:
+        raise TypeError("dst must be a 2-byte CUDA tensor of at least rows * ld elements")
+    _span_ok(src, [(rows - 1) * s_row + (K - 1) * s_k, 0], "src")
+    _check(_load().mslice_nn_pack_bf16(ctypes.c_void_p(src.data_ptr()), int(s_row), int(s_k), int(rows), int(K),
+                                       ctypes.c_void_p(dst.data_ptr()), int(ld), _stream(stream)),
+           "mslice_nn_pack_bf16")
+
+
+def mslice_nn_gemm_bf16(M, N, K, A, lda, B, ldb, C, ldc, bias=None, relu=False, beta=0.0, stream=None):
+    """C[m][n] = beta C[m][n] + sum_k A[m][k] B[n][k] (+ bias[n]) (ReLU) on the tcgen05 tensor cores:
+    A [M][lda] and B [N][ldb] BF16 (K contiguous, lda and ldb multiples of 8), C float32 [M][ldc]."""
+    for t, w, rows, ld in ((A, "A", M, lda), (B, "B", N, ldb)):
+        if not isinstance(t, torch.Tensor) or t.element_size() != 2 or not t.is_cuda or t.numel() < rows * ld:
+            raise TypeError("%s must be a 2-byte CUDA tensor of at least %d x %d elements" % (w, rows, ld))
+    if not isinstance(C, torch.Tensor) or C.dtype != torch.float32 or not C.is_cuda:
+        raise TypeError("C must be a float32 CUDA tensor")
+    _span_ok(C, [(M - 1) * ldc + N - 1], "C")
+    if bias is not None and (bias.dtype != torch.float32 or bias.numel() < N):
+        raise ValueError("bias must have N float32 elements")
+    _check(_load().mslice_nn_gemm_bf16(
+        int(M), int(N), int(K), ctypes.c_void_p(A.data_ptr()), int(lda), ctypes.c_void_p(B.data_ptr()), int(ldb),
+        ctypes.c_void_p(C.data_ptr()), int(ldc), ctypes.c_void_p(bias.data_ptr()) if bias is not None else None,
+        int(bool(relu)), float(beta), _stream(stream)), "mslice_nn_gemm_bf16")
+
+
+def mslice_nn_gemm_bf16_status(stream=None) -> int:
+    return int(_load().mslice_nn_gemm_bf16_status(_stream(stream)))
 
 
 def mslice_nn_space_to_depth(x, out, B, H, W, C, p, inverse=False, stream=None):

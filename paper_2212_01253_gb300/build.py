@@ -49,6 +49,7 @@ def _units():
              (os.path.join(CSRC, "mslice_recon.cu"), os.path.join(BUILD_DIR, "mslice_recon.o"), inc),
              (os.path.join(CSRC, "mslice_nn.cu"), os.path.join(BUILD_DIR, "mslice_nn.o"), inc),
              (os.path.join(CSRC, "mslice_rotate.cu"), os.path.join(BUILD_DIR, "mslice_rotate.o"), inc),
+             (os.path.join(CSRC, "mslice_tc.cu"), os.path.join(BUILD_DIR, "mslice_tc.o"), inc),
              (os.path.join(CSRC, "mslice_generic.cu"), os.path.join(BUILD_DIR, "generic_paraxial.o"),
               inc + ["-DMS_AS=0"]),
              (os.path.join(CSRC, "mslice_generic.cu"), os.path.join(BUILD_DIR, "generic_angular.o"),

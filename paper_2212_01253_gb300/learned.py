@@ -10,12 +10,17 @@ coarse grid, mapped onto the multislice grid (E), pushed through
 ``mslice_forward`` in per-structure batches, and turned into network inputs
 with Poisson-amplitude noise.  Every step runs in libmslice kernels:
 
-* layers: ``mslice_nn_space_to_depth`` (patch permutation) + ``mslice_nn_gemm``
-  (BF16 operands, FP32 accumulation on the tensor cores, fused bias and ReLU);
+* layers: ``mslice_nn_space_to_depth`` (patch permutation) + a GEMM with BF16
+  operands and FP32 accumulation, fused bias and ReLU: the forward and the
+  input gradient of dense enough layers (``_use_tc``) run on the tcgen05
+  tensor cores (``mslice_nn_gemm_bf16``, activations packed to BF16
+  by ``mslice_nn_pack_bf16``, weights from BF16 copies refreshed after every
+  ADAM step); the rest, and the weight gradients (long k, split over CTAs),
+  run ``mslice_nn_gemm``;
 * loss: ``mslice_nn_sigmoid_mse``; backward: the same GEMM with transposed
   strides, ``mslice_nn_relu_backward``; optimiser: ``mslice_adam_step`` over
-  the flat FP32 master parameters (weights are rounded to BF16 inside the
-  GEMM, so FP32 is the master copy).
+  the flat FP32 master parameters (FP32 is the master copy; the GEMMs read
+  weights rounded to BF16, nearest even, either way).
 
 Architecture (``arch`` dict): ``in_hw`` detector side; ``enc`` list of
 (p, c_out) patch convolutions (kernel = stride = p, ReLU) down to an 8 x 8 map;
@@ -41,6 +46,24 @@ AU_BETA = 4.9e-6
 # ~4.5M parameters: 256^2 detector -> 64^3 coarse volume
 ARCH_256 = dict(in_hw=256, enc=[(4, 32), (2, 64), (2, 128), (2, 256)], latent=128, dec_c0=256,
                 dec=[(2, 64), (2, 32), (2, 64)])
+
+
+# GEMMs with at least this many rows, this long a reduction and this many
+# output columns use the tcgen05 path (128 x 256 tiles); thinner ones are
+# bound by memory, where packing the activations to BF16 costs more than the
+# tensor cores save (ARCH_256 at batch 64: 2.12 ms per step on mslice_nn_gemm,
+# 2.34 ms with every layer of >= 1024 rows on the tcgen05 path)
+TC_MIN_ROWS = 1024
+TC_MIN_K = 256
+TC_MIN_N = 128
+
+
+def _use_tc(rows, n_out, k_red):
+    return rows >= TC_MIN_ROWS and k_red >= TC_MIN_K and n_out >= TC_MIN_N
+
+
+def _ld8(n):
+    return (int(n) + 7) // 8 * 8
 
 
 def layers_of(arch):
@@ -107,6 +130,18 @@ class EncoderDecoder:
                      B.mslice_nn_gemm_workspace(L["N"], L["K"], rows),
                      B.mslice_nn_gemm_workspace(1, L["N"], rows),
                      B.mslice_nn_gemm_workspace(rows, L["K"], L["N"]))
+        # BF16 operands of the tcgen05 path: weights W [N][K] and W^T [K][N]
+        # (refreshed after every ADAM step), and per-call activation packs
+        bf = dict(dtype=torch.bfloat16, device=self.dev)
+        pack = 8
+        for L in self.layers:
+            rows = self._rows(L, Bm)
+            L["ldK"], L["ldN"] = _ld8(L["K"]), _ld8(L["N"])
+            L["w16"] = torch.empty(L["N"] * L["ldK"], **bf)
+            L["w16t"] = torch.empty(L["K"] * L["ldN"], **bf)
+            pack = max(pack, rows * max(L["ldK"], L["ldN"]))
+        self.pack16 = torch.empty(pack, **bf)
+        self.refresh_bf16()
         self.dA0 = torch.empty(Bm * arch["in_hw"] ** 2, **f32)
         self.ws = torch.empty(max(ws, 16) // 4 + 4, **f32)
         self.out_numel = self.side * self.side * self.depth
@@ -124,6 +159,22 @@ class EncoderDecoder:
 
     def _gemm(self, M, N, K, A, sam, sak, Bt, sbn, sbk, C, ldc, bias=None, relu=False):
         B.mslice_nn_gemm(M, N, K, A, sam, sak, Bt, sbn, sbk, C, ldc, bias, relu, 0.0, self.ws)
+
+    def refresh_bf16(self):
+        """BF16 copies of every layer's weights and their transposes (after
+        ADAM steps this runs by itself; call it after writing theta directly)."""
+        for L in self.layers:
+            N, K = L["N"], L["K"]
+            B.mslice_nn_pack_bf16(L["w"], K, 1, N, K, L["w16"], L["ldK"])
+            B.mslice_nn_pack_bf16(L["w"], 1, K, K, N, L["w16t"], L["ldN"])
+
+    def _gemm_w(self, M, N, K, X, W16, ldw, C, bias=None, relu=False):
+        """C[M][N] = X[M][K] W^T (+ bias) (ReLU): X float32 row-major, W16 the
+        layer's BF16 copy [N][ldw], on the tcgen05 tensor cores."""
+        ldx = _ld8(K)
+        X16 = self.pack16[:M * ldx]
+        B.mslice_nn_pack_bf16(X, K, 1, M, K, X16, ldx)
+        B.mslice_nn_gemm_bf16(M, N, K, X16, ldx, W16, ldw, C, N, bias, relu, 0.0)
 
     def forward(self, x, nb=None):
         """x: features [nb][in_hw][in_hw] (float32, contiguous) -> pre-sigmoid
@@ -143,7 +194,10 @@ class EncoderDecoder:
                 X = a[:rows * L["K"]]
             L["Xin"] = X
             Y = L["Y"][:rows * L["N"]]
-            self._gemm(rows, L["N"], L["K"], X, L["K"], 1, L["w"], L["K"], 1, Y, L["N"], L["b"], L["relu"])
+            if _use_tc(rows, L["N"], L["K"]):
+                self._gemm_w(rows, L["N"], L["K"], X, L["w16"], L["ldK"], Y, L["b"], L["relu"])
+            else:
+                self._gemm(rows, L["N"], L["K"], X, L["K"], 1, L["w"], L["K"], 1, Y, L["N"], L["b"], L["relu"])
             if L["kind"] == "dec":
                 so = L["side"] * L["p"]
                 Aout = L["A"][:nb * so * so * L["cout"]]
@@ -181,7 +235,10 @@ class EncoderDecoder:
                 break
             # dX[m][k] = sum_n dZ[m][n] W[n][k]
             dX = L["dX"][:rows * K]
-            self._gemm(rows, K, N, dZ, N, 1, L["w"], 1, K, dX, K)
+            if _use_tc(rows, K, N):
+                self._gemm_w(rows, K, N, dZ, L["w16t"], L["ldN"], dX)
+            else:
+                self._gemm(rows, K, N, dZ, N, 1, L["w"], 1, K, dX, K)
             if L["kind"] == "enc":
                 s, hp = L["side"], L["side"] // L["p"]
                 dA = self.layers[li - 1]["dY"] if li > 0 else self.dA0
@@ -206,6 +263,7 @@ class EncoderDecoder:
     def adam(self, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
         self.t += 1
         B.mslice_adam_step(self.theta, self.m, self.v, self.grad, lr, b1, b2, eps, self.t, -3.0e38, 3.0e38)
+        self.refresh_bf16()
 
     def predict(self, x, nb=None, hi=AU_DELTA):
         """Coarse volume theta = hi * sigmoid(net(x)), [nb][cx][cz][cy]."""

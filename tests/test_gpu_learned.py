@@ -140,13 +140,21 @@ def test_sigmoid_mse_vs_oracle():
 SMALL = dict(in_hw=32, enc=[(2, 8), (2, 16)], latent=24, dec_c0=12, dec=[(2, 8), (2, 6)])
 
 
-def test_network_forward_and_gradients_vs_oracle():
+@pytest.mark.parametrize("tensor_cores", [False, True])
+def test_network_forward_and_gradients_vs_oracle(tensor_cores, monkeypatch):
+    """Forward, loss and every parameter gradient against the oracle, with the
+    layers' forward and input-gradient GEMMs on mslice_nn_gemm or, with the
+    thresholds at 1, all on the tcgen05 path (BF16 weight copies)."""
+    from paper_2212_01253_gb300 import learned
     from paper_2212_01253_gb300.learned import EncoderDecoder
+    for name in ("TC_MIN_ROWS", "TC_MIN_K", "TC_MIN_N"):
+        monkeypatch.setattr(learned, name, 1 if tensor_cores else 1 << 30)
     rng = np.random.default_rng(6)
     net = EncoderDecoder(SMALL, max_batch=4)
     assert net.n_params == onn.n_params(SMALL)
     th = (rng.standard_normal(net.n_params) * 0.2).astype(np.float32)
     net.theta.copy_(torch.from_numpy(th))
+    net.refresh_bf16()
     x = rng.standard_normal((3, 32, 32)).astype(np.float32)
     tgt = (rng.random((3, 32, 32, 6)) < 0.3).astype(np.float32)
     rl = net.loss_grad(G.dev(x, np.float32), G.dev(tgt, np.float32), nb=3)

@@ -148,6 +148,64 @@ __global__ void __launch_bounds__(256) k_rotate(const float2* __restrict__ in, f
     }
 }
 
+// The forward without yaw (RotMap::y_identity): the y stencil is the identity
+// (lower index m, weight 0) and the x and z stencils do not depend on m, so
+// every voxel of lab row (j, l) takes the same four sample rows with the same
+// four weights.  One warp per lab row, the stencil formed once, four columns
+// per lane in flight; the sum w000 p00 + w001 p01 + w100 p10 + w101 p11 is
+// k_rotate's with p = v0 + 0 (v1 - v0) = v0, the same value for finite data.
+__global__ void __launch_bounds__(256) k_rotate_xz(const float2* __restrict__ in, float2* __restrict__ out,
+                                                   const RotMap R) {
+    const int lane = threadIdx.x & 31;
+    const unsigned rows = (unsigned)R.n[0] * (unsigned)R.n[1];
+    const unsigned warps = gridDim.x * (blockDim.x >> 5);
+    const int ny = R.n[2];
+    for (unsigned row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); row < rows; row += warps) {
+        const unsigned j = row / (unsigned)R.n[1], l = row - j * (unsigned)R.n[1];
+        int ri_k = 0;
+        float rf_k = 0.f;
+        if (lane < 3) {
+            const double b = lane == 0 ? R.b[0] : (lane == 1 ? R.b[1] : R.b[2]);
+            const double aj = lane == 0 ? R.A[0][0] : (lane == 1 ? R.A[1][0] : R.A[2][0]);
+            const double al = lane == 0 ? R.A[0][1] : (lane == 1 ? R.A[1][1] : R.A[2][1]);
+            const double f = fma(al, (double)l, fma(aj, (double)j, b));
+            const double fl = floor(f);
+            ri_k = (int)fl;
+            rf_k = (float)(f - fl);
+        }
+        int ri[3];
+        float rf[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            ri[k] = __shfl_sync(0xffffffffu, ri_k, k);
+            rf[k] = __shfl_sync(0xffffffffu, rf_k, k);
+        }
+        const Stencil S = stencil(R, ri, rf, 0);   // x and z parts: the same for every column
+        const float2 *p00 = in + S.a00, *p01 = in + S.a01, *p10 = in + S.a10, *p11 = in + S.a11;
+        float2* o = out + (size_t)row * ny;
+        for (int m0 = 0; m0 < ny; m0 += 128) {
+            float2 v[4][4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int m = m0 + 32 * c + lane;
+                if (m < ny) {
+                    v[c][0] = __ldg(p00 + m);
+                    v[c][1] = __ldg(p01 + m);
+                    v[c][2] = __ldg(p10 + m);
+                    v[c][3] = __ldg(p11 + m);
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int m = m0 + 32 * c + lane;
+                if (m < ny)
+                    o[m] = make_float2(S.w000 * v[c][0].x + S.w001 * v[c][1].x + S.w100 * v[c][2].x + S.w101 * v[c][3].x,
+                                       S.w000 * v[c][0].y + S.w001 * v[c][1].y + S.w100 * v[c][2].y + S.w101 * v[c][3].y);
+            }
+        }
+    }
+}
+
 // weight of sample index s in the stencil of lab column m along one axis:
 // axis_stencil's arithmetic with the indices kept as exact integers in FP32
 // (|index| < 2^24), so that no conversion is needed (ri, m, n, s as floats)
@@ -331,7 +389,7 @@ __global__ void __launch_bounds__(256) k_rotate_gather(const float2* __restrict_
 // four column chunks at a time, every row's loads before the sums
 template <int CNT>
 __device__ __forceinline__ void sum_rows(const float2* __restrict__ g_lab, float2* __restrict__ dst,
-                                         const unsigned (&lrow)[8], const float (&lw)[8], int ny, int nc, int lane,
+                                         const unsigned (&lrow)[4], const float (&lw)[4], int ny, int nc, int lane,
                                          bool first) {
     for (int c0 = 0; c0 < nc; c0 += 4) {
         float2 g[CNT > 0 ? CNT : 1][4];
@@ -364,7 +422,7 @@ __device__ __forceinline__ void sum_rows(const float2* __restrict__ g_lab, float
 // all the row's columns (lane c holds columns c, c + 32, ...).  The candidate
 // rows, their weights and the order of the sum are those of k_rotate_gather,
 // which gives bitwise the same sums (up to the sign of zero sums).
-__global__ void __launch_bounds__(256) k_rotate_gather_xz(const float2* __restrict__ g_lab,
+__global__ void __launch_bounds__(256, 3) k_rotate_gather_xz(const float2* __restrict__ g_lab,
                                                           float2* __restrict__ g_sample, const RotMap R) {
     const int lane = threadIdx.x & 31;
     const unsigned rows = (unsigned)R.n[0] * (unsigned)R.n[1];
@@ -404,17 +462,17 @@ __global__ void __launch_bounds__(256) k_rotate_gather_xz(const float2* __restri
         const int dx0 = (int)fmaxf(ceilf(xlo - tol), (float)-sx), dx1 = (int)fminf(floorf(xhi + tol), (float)(ns - 1 - sx));
         const int dz0 = (int)fmaxf(ceilf(zlo - tol), (float)-sz), dz1 = (int)fminf(floorf(zhi + tol), (float)(nz - 1 - sz));
         float2* dst = g_sample + (size_t)row * ny + lane;
-        // the contributing rows (nonzero weight) in candidate order, eight at
+        // the contributing rows (nonzero weight) in candidate order, four at
         // a time (2 to 4 in all away from the faces; a sample row on an x or z
         // face takes every lab row past that face), each batch summed onto
         // the previous batches' sums
         int dx = dz0 <= dz1 ? dx0 : dx1 + 1, dz = dz0;   // an empty z range: no candidates
         bool first = true;
         for (;;) {
-            unsigned lrow[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
-            float lw[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            unsigned lrow[4] = {0u, 0u, 0u, 0u};
+            float lw[4] = {0.f, 0.f, 0.f, 0.f};
             int cnt = 0;
-            while (dx <= dx1 && cnt < 8) {
+            while (dx <= dx1 && cnt < 4) {
                 const float rfx = rf[0] + R.Af[0][0] * (float)dx + R.Af[0][1] * (float)dz;
                 const float rfz = rf[1] + R.Af[1][0] * (float)dx + R.Af[1][1] * (float)dz;
                 const float wx = axis_weight(rif[0], rfx, R.hi[0], R.lo[0], 0.f, nsf, sxf);
@@ -423,7 +481,7 @@ __global__ void __launch_bounds__(256) k_rotate_gather_xz(const float2* __restri
                 if (wt != 0.f) {   // uniform over the warp
                     const unsigned r = (unsigned)(sx + dx) * (unsigned)nz + (unsigned)(sz + dz);
 #pragma unroll
-                    for (int k = 0; k < 8; ++k) {
+                    for (int k = 0; k < 4; ++k) {
                         if (k == cnt) {
                             lrow[k] = r;
                             lw[k] = wt;
@@ -439,11 +497,7 @@ __global__ void __launch_bounds__(256) k_rotate_gather_xz(const float2* __restri
                 case 1: sum_rows<1>(g_lab, dst, lrow, lw, ny, nc, lane, first); break;
                 case 2: sum_rows<2>(g_lab, dst, lrow, lw, ny, nc, lane, first); break;
                 case 3: sum_rows<3>(g_lab, dst, lrow, lw, ny, nc, lane, first); break;
-                case 4: sum_rows<4>(g_lab, dst, lrow, lw, ny, nc, lane, first); break;
-                case 5: sum_rows<5>(g_lab, dst, lrow, lw, ny, nc, lane, first); break;
-                case 6: sum_rows<6>(g_lab, dst, lrow, lw, ny, nc, lane, first); break;
-                case 7: sum_rows<7>(g_lab, dst, lrow, lw, ny, nc, lane, first); break;
-                default: sum_rows<8>(g_lab, dst, lrow, lw, ny, nc, lane, first); break;
+                default: sum_rows<4>(g_lab, dst, lrow, lw, ny, nc, lane, first); break;
             }
             first = false;
             if (dx > dx1) break;
@@ -545,7 +599,10 @@ int launch(const mslice_params* p, double alpha, double psi, const double* c, co
         else
             k_rotate_gather<<<blocks, 256, 0, st>>>((const float2*)in, (float2*)out, R);
     } else {
-        k_rotate<<<blocks, 256, 0, st>>>((const float2*)in, (float2*)out, R);
+        if (R.y_identity)
+            k_rotate_xz<<<blocks, 256, 0, st>>>((const float2*)in, (float2*)out, R);
+        else
+            k_rotate<<<blocks, 256, 0, st>>>((const float2*)in, (float2*)out, R);
     }
     return cudaGetLastError() == cudaSuccess ? MSLICE_OK : MSLICE_ELAUNCH;
 }

@@ -4,7 +4,8 @@
 // operand tiles moved by TMA (cp.async.bulk.tensor, 128-byte swizzle, this
 // GPU's memory only, no multicast) through a 4-stage mbarrier pipeline.
 //
-// One CTA of 4 warps per 128 x 256 output tile: lane 0 of warp 0 issues the
+// One CTA of 4 warps per 128 x 256 output tile (tiles in groups of 8 row
+// blocks, for L2 reuse): lane 0 of warp 0 issues the
 // TMA loads, lane 0 of warp 1 issues the MMAs (4 per 64-wide k step) and
 // commits each stage back to the loader, and all four warps read the
 // accumulator out of tensor memory (warp w owns rows 32w..32w+31) for the
@@ -26,6 +27,7 @@ constexpr int kBM = 128, kBN = 256, kBK = 64, kStages = 4;
 constexpr int kStageA = kBM * kBK * 2, kStageB = kBN * kBK * 2;   // bytes per stage
 constexpr int kSmemBytes = kStages * (kStageA + kStageB) + 1024;   // + 1024 for the alignment of the tiles
 constexpr int kTmemCols = 256;                                      // FP32 accumulator, one column per n
+constexpr int kGroupM = 8;                                          // row blocks per group of the tile order
 constexpr unsigned long long kWaitNs = 1000000000ull;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -172,7 +174,15 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tc(const __grid_constant__ CUte
     __shared__ int s_fail;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t tiles = (smem_u32(smem_raw) + 1023u) & ~1023u;   // 1024-byte aligned for the swizzle atoms
-    const int m0 = blockIdx.y * kBM, n0 = blockIdx.x * kBN;
+    // tile order: CTAs in launch order walk groups of kGroupM row blocks, all
+    // column blocks of a group before the next, so that the tiles in flight
+    // at once share a few A row blocks and a band of B column blocks in L2
+    const int nbn = gridDim.x, nbm = gridDim.y;
+    const int lin = blockIdx.y * nbn + blockIdx.x;
+    const int first_m = (lin / (kGroupM * nbn)) * kGroupM;
+    const int gm = nbm - first_m < kGroupM ? nbm - first_m : kGroupM;
+    const int within = lin - first_m * nbn;
+    const int m0 = (first_m + within % gm) * kBM, n0 = (within / gm) * kBN;
     const int kt_n = (K + kBK - 1) / kBK;
 
     if (threadIdx.x == 0) {

@@ -77,3 +77,25 @@ def test_shrinkwrap_workspace_size_on_host(lib):
     lib.mslice_shrinkwrap_workspace.restype = ctypes.c_size_t
     lib.mslice_shrinkwrap_workspace.argtypes = [ctypes.c_size_t]
     assert lib.mslice_shrinkwrap_workspace(216) >= 2 * 216 * 4
+
+
+def test_tensor_core_gemm_validates_arguments_on_host(lib):
+    """mslice_nn_gemm_bf16 and mslice_nn_pack_bf16 refuse bad sizes, strides
+    and alignments before any device work (the pointers are never read)."""
+    vp, ll, ci = ctypes.c_void_p, ctypes.c_longlong, ctypes.c_int
+    f = lib.mslice_nn_gemm_bf16
+    f.argtypes = [ci, ci, ci, vp, ll, vp, ll, vp, ll, vp, ci, ctypes.c_float, vp]
+    f.restype = ci
+    A, Bm, C = 0x100000, 0x200000, 0x300000     # 16-byte aligned, never dereferenced
+    assert f(0, 256, 64, A, 64, Bm, 64, C, 256, None, 0, 0.0, None) == -1        # M < 1
+    assert f(128, 256, 64, A, 60, Bm, 64, C, 256, None, 0, 0.0, None) == -1      # lda < K
+    assert f(128, 256, 64, A, 68, Bm, 64, C, 256, None, 0, 0.0, None) == -1      # lda not a multiple of 8
+    assert f(128, 256, 64, A + 8, 64, Bm, 64, C, 256, None, 0, 0.0, None) == -1  # A not 16-byte aligned
+    assert f(128, 256, 64, A, 64, Bm, 64, C, 200, None, 0, 0.0, None) == -1      # ldc < N
+    assert f(128, 256, 64, A, 64, None, 64, C, 256, None, 0, 0.0, None) == -1    # null B
+    g = lib.mslice_nn_pack_bf16
+    g.argtypes = [vp, ll, ll, ci, ci, vp, ll, vp]
+    g.restype = ci
+    assert g(A, 64, 1, 128, 64, Bm, 60, None) == -1      # ld < K
+    assert g(None, 64, 1, 128, 64, Bm, 64, None) == -1   # null source
+    assert g(A, 64, 1, 128, 64, Bm + 1, 64, None) == -1  # odd destination
